@@ -1,0 +1,168 @@
+"""Seeded synthetic snapshot matrices shared by the tests, the smoke check and
+the benchmark.
+
+This module holds input construction only: none of the POD method's
+arithmetic (no mean removal, no QR of the snapshot matrix, no SVD) lives
+here.  Library primitives (numpy/torch GEMM, and a library QR used only to
+draw random orthonormal factors) build the inputs.  The CUDA library and the
+oracle both consume what it returns; neither is imported here.
+
+Workloads (N gridpoints x M snapshots, column-major / Fortran order):
+
+* ``waves``: a wake-like field of traveling waves
+  ``f0(x) + sum_j a_j sin(k_j x - w_j t) + noise`` on ``x_n = 2 pi n / N``,
+  ``t_m = m dt`` with ``w_j = 2 pi q_j / (M dt)``, so that with distinct
+  integer ``k_j < N/2`` and ``q_j < M/2`` the sampled sines and cosines are
+  orthogonal and, noise-free, each wave contributes the singular value
+  ``a_j sqrt(N M) / 2`` twice (a closed form the tests use).
+* ``known_spectrum``: ``X = diag(w)^(-1/2) Q1 diag(s) Q2^T`` with seeded
+  random orthonormal ``Q1`` (N x M) and Haar ``Q2`` (M x M), so the weighted
+  snapshot matrix ``diag(sqrt w) X`` has singular values ``s`` exactly (up
+  to construction rounding).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# ----------------------------------------------------------------------------
+# wave parameters of the two wave workloads
+# ----------------------------------------------------------------------------
+
+def wave_params(n_waves: int, amp: str = "geometric"):
+    """(a_j, k_j, q_j) for the wave workloads.
+
+    geometric: a_j = 2^-j (16384 x 64 workload, 8 waves)
+    powerlaw:  a_j = (1 + j)^(-5/6) (10^7 x 1808 workload, 64 waves)
+    """
+    j = np.arange(n_waves, dtype=np.float64)
+    if amp == "geometric":
+        a = 2.0 ** (-j)
+        k = 1 + 2 * np.arange(n_waves)
+        q = 1 + 3 * np.arange(n_waves)
+    elif amp == "powerlaw":
+        a = (1.0 + j) ** (-5.0 / 6.0)
+        k = 1 + 2 * np.arange(n_waves)
+        q = 1 + 7 * np.arange(n_waves)
+    else:
+        raise ValueError(amp)
+    return a, k.astype(np.int64), q.astype(np.int64)
+
+
+def waves(N: int, M: int, n_waves: int = 8, amp: str = "geometric", noise: float = 1e-3,
+          seed: int = 1, dt: float = 0.2, dtype=np.float64) -> np.ndarray:
+    """Traveling-wave snapshot matrix (numpy, Fortran order)."""
+    a, k, q = wave_params(n_waves, amp)
+    x = 2.0 * np.pi * np.arange(N, dtype=np.float64) / N
+    t = dt * np.arange(M, dtype=np.float64)
+    omega = 2.0 * np.pi * q / (M * dt)
+    # sin(kx - wt) = sin(kx) cos(wt) - cos(kx) sin(wt): a rank-2J product
+    Fx = np.concatenate([np.sin(np.outer(x, k)), -np.cos(np.outer(x, k))], axis=1)  # N x 2J
+    Gt = np.concatenate([np.cos(np.outer(omega, t)), np.sin(np.outer(omega, t))], axis=0)  # 2J x M
+    Gt = Gt * np.concatenate([a, a])[:, None]
+    X = Fx @ Gt
+    X += (1.0 + 0.5 * np.cos(x))[:, None]
+    if noise > 0.0:
+        rng = np.random.default_rng(seed)
+        X += noise * rng.standard_normal((N, M))
+    return np.asfortranarray(X.astype(dtype))
+
+
+def waves_torch(N: int, M: int, n_waves: int, amp: str, noise: float, seed: int, device,
+                dtype=None, dt: float = 0.2, row_chunk: int = 1 << 22):
+    """Device-side version of :func:`waves` for large N (column-major result:
+    a torch tensor of shape (M, N) whose transpose view is the N x M matrix)."""
+    import torch
+    dtype = dtype or torch.float64
+    a, k, q = wave_params(n_waves, amp)
+    omega = 2.0 * np.pi * q / (M * dt)
+    t = dt * np.arange(M, dtype=np.float64)
+    Gt = np.concatenate([np.cos(np.outer(omega, t)), np.sin(np.outer(omega, t))], axis=0)
+    Gt = torch.tensor(Gt * np.concatenate([a, a])[:, None], dtype=torch.float64, device=device)
+    kk = torch.tensor(k, dtype=torch.float64, device=device)
+    XT = torch.empty((M, N), dtype=dtype, device=device)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    for r0 in range(0, N, row_chunk):
+        r1 = min(N, r0 + row_chunk)
+        x = 2.0 * math.pi * torch.arange(r0, r1, dtype=torch.float64, device=device) / N
+        kx = torch.outer(x, kk)
+        Fx = torch.cat([torch.sin(kx), -torch.cos(kx)], dim=1)
+        blk = Fx @ Gt + (1.0 + 0.5 * torch.cos(x))[:, None]
+        if noise > 0.0:
+            blk += noise * torch.randn(blk.shape, dtype=torch.float64, device=device, generator=gen)
+        XT[:, r0:r1] = blk.T.to(dtype)
+    return XT
+
+
+# ----------------------------------------------------------------------------
+# known-spectrum workload
+# ----------------------------------------------------------------------------
+
+def spectrum(M: int, decades: float = 6.0) -> np.ndarray:
+    """s_i = 10^(-decades * i / (M - 1)), i = 0..M-1."""
+    i = np.arange(M, dtype=np.float64)
+    return 10.0 ** (-decades * i / max(M - 1, 1))
+
+
+def log_uniform_weights(N: int, seed: int, lo: float = 1e-3, hi: float = 1.0) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return 10.0 ** rng.uniform(math.log10(lo), math.log10(hi), size=N)
+
+
+def haar_orthogonal(M: int, seed: int) -> np.ndarray:
+    """Haar-distributed M x M orthogonal matrix (library QR of a Gaussian with
+    the signs of R's diagonal moved into Q)."""
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((M, M))
+    Q, R = np.linalg.qr(G)
+    return Q * np.sign(np.diag(R))[None, :]
+
+
+def orthonormal_columns(N: int, M: int, seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((N, M))
+    Q, R = np.linalg.qr(G)
+    return Q * np.sign(np.diag(R))[None, :]
+
+
+def known_spectrum(N: int, M: int, s=None, weights: bool = True, seeds=(2, 3, 4),
+                   dtype=np.float64):
+    """X = diag(w)^(-1/2) Q1 diag(s) Q2^T; returns (X, w or None, s)."""
+    if s is None:
+        s = spectrum(M)
+    Q1 = orthonormal_columns(N, M, seeds[0])
+    Q2 = haar_orthogonal(M, seeds[1])
+    Y = (Q1 * s[None, :]) @ Q2.T
+    w = log_uniform_weights(N, seeds[2]) if weights else None
+    X = Y / np.sqrt(w)[:, None] if weights else Y
+    return np.asfortranarray(X.astype(dtype)), w, np.asarray(s, dtype=np.float64)
+
+
+def known_spectrum_torch(N: int, M: int, device, s=None, weights: bool = True, seeds=(2, 3, 4),
+                         dtype=None):
+    """Device-side :func:`known_spectrum` for large N.  Returns (XT, w, s) with
+    XT of shape (M, N) (so XT.T is the column-major N x M matrix)."""
+    import torch
+    dtype = dtype or torch.float64
+    if s is None:
+        s = spectrum(M)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seeds[0])
+    G = torch.randn((N, M), dtype=torch.float64, device=device, generator=gen)
+    Q1, R1 = torch.linalg.qr(G)
+    Q1 *= torch.sign(torch.diagonal(R1))[None, :]
+    del G, R1
+    Q2 = torch.tensor(haar_orthogonal(M, seeds[1]), dtype=torch.float64, device=device)
+    st = torch.tensor(s, dtype=torch.float64, device=device)
+    Y = (Q1 * st[None, :]) @ Q2.T
+    del Q1
+    if weights:
+        w = torch.tensor(log_uniform_weights(N, seeds[2]), dtype=torch.float64, device=device)
+        Y /= torch.sqrt(w)[:, None]
+    else:
+        w = None
+    XT = Y.T.contiguous().to(dtype)
+    del Y
+    return XT, w, np.asarray(s, dtype=np.float64)
