@@ -1,0 +1,186 @@
+/*
+ * pylom.h -- C ABI of the GB300 (sm_103a) POD / TSQR-SVD library.
+ *
+ * The library computes the proper orthogonal decomposition of a tall-skinny
+ * snapshot matrix X (N gridpoints x M snapshots) the way pyLOM does
+ * (Eiximeno et al., arXiv 2405.15529, Sec. 3.1 and Algs. 1, 2 and 4):
+ *   temporal mean removal (Alg. 2) and optional sqrt(cell-volume) weights,
+ *   a TSQR -- blocked Householder QR of row blocks ("leaves") followed by a
+ *   binary-tree reduction of the stacked R factors (Alg. 1; on one GPU the
+ *   tree runs across thread blocks),
+ *   an SVD of the small M x M R (Eq. svdqr2),
+ *   and the modes U = Q U_r (Eq. svdqr3).
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are column-major with an explicit leading dimension (ld >= rows).
+ *   - Every array argument is DEVICE memory owned by the caller, unless the
+ *     comment says "host".  The library never allocates: each call that needs
+ *     scratch takes a caller-provided device workspace whose size comes from
+ *     the matching *_workspace_size query.  Workspaces must be 256-byte
+ *     aligned and must not be shared by calls that may overlap on the GPU.
+ *   - Calls are asynchronous and stream-ordered on `stream` (a cudaStream_t
+ *     passed as void*; NULL = the legacy default stream).
+ *   - Arguments are validated on the host before anything is launched; an
+ *     invalid call returns an error status and writes no output.
+ *   - Conditions only the device can see (non-finite input, Jacobi not
+ *     converged, a bounded wait that ran out) are recorded in the workspace
+ *     header and read back with pylom_workspace_status().
+ *   - A failed CUDA launch returns PYLOM_ERR_CUDA; pylom_last_error() gives
+ *     the message (thread-local, valid until the next call on the thread).
+ */
+#ifndef PYLOM_H
+#define PYLOM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PYLOM_OK = 0,
+  PYLOM_ERR_ARG = 1,         /* null pointer, bad enum, bad leading dimension */
+  PYLOM_ERR_SHAPE = 2,       /* N < M, M < 1, leaf height < M, r_max out of range */
+  PYLOM_ERR_WORKSPACE = 3,   /* workspace too small or misaligned */
+  PYLOM_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+  PYLOM_ERR_NONFINITE = 5,   /* device: the input holds NaN or Inf */
+  PYLOM_ERR_NOCONV = 6,      /* device: Jacobi SVD hit max_sweeps */
+  PYLOM_ERR_TIMEOUT = 7,     /* device: a bounded inter-block wait ran out */
+  PYLOM_ERR_UNSUPPORTED = 8  /* valid request this build does not implement */
+} pylom_status;
+
+typedef enum { PYLOM_F32 = 0, PYLOM_F64 = 1, PYLOM_C64 = 2, PYLOM_C128 = 3 } pylom_dtype;
+
+/* Arithmetic of the hot path.  FP64: every step in binary64 (trailing
+ * updates and the modes product on the FP64 tensor pipe, mma.sync.m8n8k4). */
+typedef enum { PYLOM_PREC_FP64 = 0, PYLOM_PREC_MIXED_3XTF32 = 1 } pylom_prec;
+
+/* Which left vectors pylom_pod returns (only differs when w != NULL).
+ * ORTHONORMAL: U_w, the left singular vectors of Y_w = diag(sqrt w) Y,
+ *              Euclidean-orthonormal.
+ * PHYSICAL:    Phi = diag(w)^(-1/2) U_w, orthonormal in the volume-weighted
+ *              inner product sum_n w_n Phi_i(n) Phi_j(n) (the discrete form of
+ *              the integral orthonormality of Sec. 2.1). */
+typedef enum { PYLOM_MODES_ORTHONORMAL = 0, PYLOM_MODES_PHYSICAL = 1 } pylom_mode_kind;
+
+/* Library version string (static storage). */
+const char* pylom_version(void);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* pylom_last_error(void);
+
+/* Number of TSQR leaves for an N-row problem with leaf height hint
+ * leaf_rows = b: P = max(1, floor(N / b)); leaf_rows = 0 picks
+ * P = max(1, min(304, floor(N / max(M, 1024)))).  Leaf i owns rows
+ * [floor(i N / P), floor((i+1) N / P)), so every leaf has >= M rows.
+ * Returns -1 on invalid arguments. */
+int64_t pylom_leaf_count(int64_t N, int64_t M, int64_t leaf_rows);
+
+/* Device status recorded in a workspace by the last call that used it.
+ * Synchronises `stream`, then returns the recorded pylom_status
+ * (PYLOM_OK if none) and, when the pointers are non-NULL, writes to HOST
+ * memory the truncation rank chosen by pylom_pod (*r) and the Jacobi sweeps
+ * used (*sweeps). */
+pylom_status pylom_workspace_status(const void* ws, void* stream, int64_t* r, int* sweeps);
+
+/* ------------------------------------------------------------------------
+ * pylom_pod -- POD of Alg. 2: Y = X - xbar 1^T (if remove_mean), weighted
+ * Y_w = diag(sqrt w) Y (if w != NULL), then Y_w = U S V^T by TSQR + small
+ * SVD + U = Q U_r (Eqs. svdqr1-svdqr3, Alg. 1), truncated by cumulative
+ * energy (Sec. 3.1).
+ *
+ *  X      in   N x M, ldx >= N, element type xtype (PYLOM_F32 or PYLOM_F64).
+ *              Not modified.
+ *  w      in   N cell volumes (> 0), or NULL for uniform weights.
+ *  remove_mean  1: subtract the per-gridpoint temporal mean (Alg. 2).
+ *  energy       keep r = min{k : sum_{i<=k} S_i^2 / sum_i S_i^2 >= energy},
+ *               capped at r_max; energy <= 0 keeps r = r_max.
+ *  r_max        1 <= r_max <= M: the columns U has room for.
+ *  mode_kind    pylom_mode_kind (see above).
+ *  leaf_rows    TSQR leaf height hint b (0 = automatic; else b >= M).
+ *  U      out  N x r_max, ldu >= N, binary64: the first r columns receive
+ *              the modes, the rest are left untouched.
+ *  S      out  M singular values, descending.
+ *  VT     out  M x M, ldvt >= M: row i is v_i^T, the temporal coefficients
+ *              of mode i (Sec. 3.1).  Each pair (u_i, v_i) is signed so that
+ *              the largest-magnitude entry of v_i is positive (lowest index
+ *              on a tie).
+ *  mean   out  N temporal means (zeros if !remove_mean), or NULL.
+ *  r_out  out  device int64: the chosen r, or NULL (also readable through
+ *              pylom_workspace_status).
+ *  prec         pylom_prec.  This build implements PYLOM_PREC_FP64.
+ *  ws, ws_bytes device workspace of at least pylom_pod_workspace_size().
+ * ------------------------------------------------------------------------ */
+size_t pylom_pod_workspace_size(int64_t N, int64_t M, int64_t leaf_rows, int64_t r_max,
+                                int xtype, int prec);
+pylom_status pylom_pod(const void* X, int64_t N, int64_t M, int64_t ldx, int xtype,
+                       const double* w, int remove_mean, double energy, int64_t r_max,
+                       int mode_kind, int64_t leaf_rows,
+                       double* U, int64_t ldu, double* S, double* VT, int64_t ldvt,
+                       double* mean, int64_t* r_out, int prec,
+                       void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * pylom_tsqr -- tall-skinny QR of Alg. 1: A = Q [R; 0] (Eq. svdqr1).
+ *  A      in   N x M, lda >= N, xtype F32 or F64 (not modified).
+ *  R      out  M x M upper triangular (zeros below the diagonal), ldr >= M.
+ *              Row signs follow the Householder convention
+ *              beta = -sign(alpha) |x| at every leaf and tree node, so R is
+ *              fixed up to row signs by A (compare R^T R or |R_ii|).
+ *  Q      out  N x M explicit orthonormal factor, ldq >= N, or NULL to skip
+ *              (the top-down broadcast pass of Alg. 1, then Q_i = Q_1i Q_w
+ *              on every leaf).
+ * ------------------------------------------------------------------------ */
+size_t pylom_tsqr_workspace_size(int64_t N, int64_t M, int64_t leaf_rows, int want_q,
+                                 int xtype, int prec);
+pylom_status pylom_tsqr(const void* A, int64_t N, int64_t M, int64_t lda, int xtype,
+                        int64_t leaf_rows, double* R, int64_t ldr, double* Q, int64_t ldq,
+                        int prec, void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * pylom_svd_small -- SVD of the small M x M factor, R = U S V^T
+ * (Eq. svdqr2), by parallel one-sided Jacobi in binary64 across thread
+ * blocks (round-robin pair ordering; a pair rotates while
+ * |a_i.a_j| > M 2^-53 |a_i| |a_j|).  Sorted descending, same sign rule as
+ * pylom_pod.  R is any M x M matrix (triangular or not), not modified.
+ *  U out M x M (ldu >= M), S out M, VT out M x M (ldvt >= M).
+ *  max_sweeps   1..64; not converging records PYLOM_ERR_NOCONV.
+ * ------------------------------------------------------------------------ */
+size_t pylom_svd_small_workspace_size(int64_t M);
+pylom_status pylom_svd_small(const double* R, int64_t M, int64_t ldr, double* U, int64_t ldu,
+                             double* S, double* VT, int64_t ldvt, int max_sweeps,
+                             void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * pylom_matmul -- local product of Alg. 4 (matmul_paral) on one device:
+ * C = op(A) B, op(A) = A (m x k, lda >= m) or A^T (A stored k x m,
+ * lda >= k); B k x n (ldb >= k); C m x n (ldc >= m).  binary64 on the FP64
+ * tensor pipe, split along k with a fixed-order reduction (deterministic).
+ * The all_reduce of Alg. 4 is the caller's (one device here).
+ * ------------------------------------------------------------------------ */
+size_t pylom_matmul_workspace_size(int64_t m, int64_t n, int64_t k);
+pylom_status pylom_matmul(int transA, const double* A, const double* B, double* C,
+                          int64_t m, int64_t n, int64_t k, int64_t lda, int64_t ldb, int64_t ldc,
+                          void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Phase profiler (measurement support; no counterpart in the paper).
+ * Between begin and end, each of the next max_calls pylom_pod calls records
+ * CUDA events on its own stream at the boundaries of its phases:
+ *   0 leaf Householder QR + tree reduction (one kernel),
+ *   1 small SVD (Jacobi + sort/sign/truncate),
+ *   2 top-down pass of the tree,
+ *   3 leaf modes product U = Q [B; 0].
+ * pylom_profile_end synchronises on the recorded events and writes to HOST
+ * memory the summed milliseconds per phase (phase_ms[PYLOM_PROFILE_PHASES])
+ * and the number of calls recorded.  Host-global state: not thread-safe.
+ * ------------------------------------------------------------------------ */
+#define PYLOM_PROFILE_PHASES 4
+pylom_status pylom_profile_begin(int max_calls);
+pylom_status pylom_profile_end(double* phase_ms, int* calls);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PYLOM_H */

@@ -1,0 +1,308 @@
+"""GB300-native POD / TSQR-SVD (the hot path of pyLOM, arXiv 2405.15529).
+
+Thin Python binding over the C ABI of ``libpylom.so`` (declared in
+``include/pylom.h``).  This module only marshals arguments: every step of the
+path (mean removal and weights, leaf Householder QR, the tree reduction of
+Alg. 1, the Jacobi SVD of R, the top-down pass and U = Q U_r) runs in the
+library's CUDA kernels.  PyTorch supplies device memory and streams.
+
+There is no CPU fallback: importing works without the library, but every
+call raises if ``libpylom.so`` has not been built or no CUDA device exists.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpylom.so")
+
+# pylom_status
+OK, ERR_ARG, ERR_SHAPE, ERR_WORKSPACE, ERR_CUDA, ERR_NONFINITE, ERR_NOCONV, ERR_TIMEOUT, \
+    ERR_UNSUPPORTED = range(9)
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_SHAPE", 3: "ERR_WORKSPACE", 4: "ERR_CUDA",
+                5: "ERR_NONFINITE", 6: "ERR_NOCONV", 7: "ERR_TIMEOUT", 8: "ERR_UNSUPPORTED"}
+# pylom_dtype / pylom_prec / pylom_mode_kind
+F32, F64, C64, C128 = 0, 1, 2, 3
+PREC_FP64, PREC_MIXED_3XTF32 = 0, 1
+MODES_ORTHONORMAL, MODES_PHYSICAL = 0, 1
+
+# Every symbol include/pylom.h declares (checked by the tests).
+EXPORTS = (
+    "pylom_version", "pylom_last_error", "pylom_leaf_count", "pylom_workspace_status",
+    "pylom_pod_workspace_size", "pylom_pod", "pylom_tsqr_workspace_size", "pylom_tsqr",
+    "pylom_svd_small_workspace_size", "pylom_svd_small", "pylom_matmul_workspace_size",
+    "pylom_matmul", "pylom_profile_begin", "pylom_profile_end",
+    "pylom_probe_scratch_bytes", "pylom_probe_fp64_peak",
+)
+PROFILE_PHASES = ("leaf_qr_tree", "svd_small", "down_pass", "modes")
+
+
+class PylomError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_i64 = ctypes.c_int64
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+_int = ctypes.c_int
+_dbl = ctypes.c_double
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libpylom.so (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    lib.pylom_version.restype = ctypes.c_char_p
+    lib.pylom_last_error.restype = ctypes.c_char_p
+    lib.pylom_leaf_count.restype = _i64
+    lib.pylom_leaf_count.argtypes = [_i64, _i64, _i64]
+    lib.pylom_workspace_status.restype = _int
+    lib.pylom_workspace_status.argtypes = [_vp, _vp, ctypes.POINTER(_i64), ctypes.POINTER(_int)]
+    lib.pylom_pod_workspace_size.restype = _sz
+    lib.pylom_pod_workspace_size.argtypes = [_i64, _i64, _i64, _i64, _int, _int]
+    lib.pylom_pod.restype = _int
+    lib.pylom_pod.argtypes = [_vp, _i64, _i64, _i64, _int, _vp, _int, _dbl, _i64, _int, _i64,
+                              _vp, _i64, _vp, _vp, _i64, _vp, _vp, _int, _vp, _sz, _vp]
+    lib.pylom_tsqr_workspace_size.restype = _sz
+    lib.pylom_tsqr_workspace_size.argtypes = [_i64, _i64, _i64, _int, _int, _int]
+    lib.pylom_tsqr.restype = _int
+    lib.pylom_tsqr.argtypes = [_vp, _i64, _i64, _i64, _int, _i64, _vp, _i64, _vp, _i64, _int,
+                               _vp, _sz, _vp]
+    lib.pylom_svd_small_workspace_size.restype = _sz
+    lib.pylom_svd_small_workspace_size.argtypes = [_i64]
+    lib.pylom_svd_small.restype = _int
+    lib.pylom_svd_small.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _int, _vp, _sz, _vp]
+    lib.pylom_matmul_workspace_size.restype = _sz
+    lib.pylom_matmul_workspace_size.argtypes = [_i64, _i64, _i64]
+    lib.pylom_matmul.restype = _int
+    lib.pylom_matmul.argtypes = [_int, _vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _i64, _vp, _sz, _vp]
+    lib.pylom_profile_begin.restype = _int
+    lib.pylom_profile_begin.argtypes = [_int]
+    lib.pylom_profile_end.restype = _int
+    lib.pylom_profile_end.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_int)]
+    lib.pylom_probe_scratch_bytes.restype = _sz
+    lib.pylom_probe_fp64_peak.restype = _int
+    lib.pylom_probe_fp64_peak.argtypes = [_int, _vp, ctypes.POINTER(ctypes.c_double), _vp]
+    _lib = lib
+    return lib
+
+
+def _raise(status: int, what: str):
+    if status != OK:
+        msg = load_library().pylom_last_error().decode(errors="replace")
+        raise PylomError(status, f"{what}: {msg}")
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: the POD path runs only on the GPU (no CPU fallback)")
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _colmajor(t):
+    """Column-major view of a 2-D tensor (copies only if needed).  Strides of
+    size-1 dimensions carry no layout information and are ignored."""
+    if t.dim() != 2:
+        raise ValueError("expected a 2-D tensor")
+    rows, cols = t.shape
+    if (rows == 1 or t.stride(0) == 1) and (cols == 1 or t.stride(1) >= rows):
+        return t
+    return t.t().contiguous().t()
+
+
+def _ld(t):
+    """Leading dimension of a column-major 2-D tensor."""
+    rows, cols = t.shape
+    return max(1, rows) if cols == 1 else t.stride(1)
+
+
+def empty_colmajor(rows: int, cols: int, dtype, device):
+    torch = _torch()
+    return torch.empty((cols, rows), dtype=dtype, device=device).t()
+
+
+def _dptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def profile_begin(max_calls: int) -> None:
+    _raise(load_library().pylom_profile_begin(int(max_calls)), "pylom_profile_begin")
+
+
+def profile_end():
+    """Summed milliseconds per phase of the profiled pylom_pod calls."""
+    arr = (ctypes.c_double * len(PROFILE_PHASES))()
+    n = _int(0)
+    _raise(load_library().pylom_profile_end(arr, ctypes.byref(n)), "pylom_profile_end")
+    return dict(zip(PROFILE_PHASES, list(arr))), int(n.value)
+
+
+def probe_fp64_peak(kind: str = "mma") -> float:
+    """Measured FP64 TFLOP/s of this GPU: kind 'mma' (tensor pipe,
+    mma.sync.m8n8k4.f64) or 'fma' (scalar FP64 FMA)."""
+    torch = _torch()
+    lib = load_library()
+    scratch = torch.empty(lib.pylom_probe_scratch_bytes(), dtype=torch.uint8, device="cuda")
+    out = ctypes.c_double(0.0)
+    st = lib.pylom_probe_fp64_peak(0 if kind == "mma" else 1, _dptr(scratch), ctypes.byref(out),
+                                   _stream(None))
+    _raise(st, "pylom_probe_fp64_peak")
+    return float(out.value)
+
+
+def leaf_count(N: int, M: int, leaf_rows: int = 0) -> int:
+    return int(load_library().pylom_leaf_count(N, M, leaf_rows))
+
+
+def workspace_status(ws, stream=None):
+    """(status, r, sweeps) recorded in a workspace; synchronises the stream."""
+    r = _i64(0)
+    sw = _int(0)
+    st = load_library().pylom_workspace_status(_dptr(ws), _stream(stream), ctypes.byref(r), ctypes.byref(sw))
+    return st, int(r.value), int(sw.value)
+
+
+@dataclass
+class PodResult:
+    U: "torch.Tensor"        # N x r (column-major view)
+    S: "torch.Tensor"        # M
+    VT: "torch.Tensor"       # M x M
+    mean: Optional["torch.Tensor"]
+    r: int
+    sweeps: int
+    workspace: "torch.Tensor"
+
+
+def pod_workspace_size(N, M, leaf_rows=0, r_max=None, xtype=F64, prec=PREC_FP64) -> int:
+    r_max = M if r_max is None else r_max
+    return int(load_library().pylom_pod_workspace_size(N, M, leaf_rows, r_max, xtype, prec))
+
+
+def pod(X, w=None, remove_mean=True, energy=0.0, r_max=None, mode_kind=MODES_ORTHONORMAL,
+        leaf_rows=0, prec=PREC_FP64, workspace=None, out=None, stream=None, check=True) -> PodResult:
+    """POD of the N x M snapshot matrix X (Alg. 2 of the paper) on the GPU.
+
+    X: CUDA tensor (float32 or float64), any 2-D layout (column-major used
+    as is).  w: N cell volumes (float64) or None.  Returns U (N x r), S, VT,
+    mean.  With check=False the call stays asynchronous and U holds r_max
+    columns (r is then read later from the workspace)."""
+    torch = _torch()
+    lib = load_library()
+    X = _colmajor(X)
+    N, M = X.shape
+    xtype = {torch.float32: F32, torch.float64: F64}.get(X.dtype)
+    if xtype is None:
+        raise TypeError("X must be float32 or float64")
+    r_max = M if r_max is None else int(r_max)
+    dev = X.device
+    if w is not None:
+        w = w.to(device=dev, dtype=torch.float64).contiguous()
+    need = lib.pylom_pod_workspace_size(N, M, leaf_rows, r_max, xtype, prec)
+    if need == 0:
+        _raise(ERR_SHAPE if prec == PREC_FP64 else ERR_UNSUPPORTED,
+               f"pylom_pod_workspace_size(N={N}, M={M}, b={leaf_rows}, r_max={r_max}, prec={prec})")
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    if out is None:
+        U = empty_colmajor(N, r_max, torch.float64, dev)
+        S = torch.empty(M, dtype=torch.float64, device=dev)
+        VT = empty_colmajor(M, M, torch.float64, dev)
+        mean = torch.empty(N, dtype=torch.float64, device=dev)
+        r_dev = torch.zeros(1, dtype=torch.int64, device=dev)
+    else:
+        U, S, VT, mean, r_dev = out
+    st = lib.pylom_pod(_dptr(X), N, M, _ld(X), xtype, _dptr(w), int(bool(remove_mean)),
+                       float(energy), r_max, int(mode_kind), int(leaf_rows), _dptr(U), _ld(U),
+                       _dptr(S), _dptr(VT), _ld(VT), _dptr(mean), _dptr(r_dev), int(prec),
+                       _dptr(workspace), workspace.numel(), _stream(stream))
+    _raise(st, "pylom_pod")
+    r, sweeps = r_max, -1
+    if check:
+        st, r, sweeps = workspace_status(workspace, stream)
+        _raise(st, "pylom_pod (device)")
+        U = U[:, :r]
+    return PodResult(U=U, S=S, VT=VT, mean=mean, r=r, sweeps=sweeps, workspace=workspace)
+
+
+def tsqr(A, leaf_rows=0, want_q=True, prec=PREC_FP64, stream=None, check=True):
+    """TSQR of Alg. 1: returns (R, Q or None)."""
+    torch = _torch()
+    lib = load_library()
+    A = _colmajor(A)
+    N, M = A.shape
+    xtype = {torch.float32: F32, torch.float64: F64}.get(A.dtype)
+    if xtype is None:
+        raise TypeError("A must be float32 or float64")
+    need = lib.pylom_tsqr_workspace_size(N, M, leaf_rows, int(want_q), xtype, prec)
+    if need == 0:
+        _raise(ERR_SHAPE, f"pylom_tsqr_workspace_size(N={N}, M={M}, b={leaf_rows})")
+    ws = torch.empty(need, dtype=torch.uint8, device=A.device)
+    R = empty_colmajor(M, M, torch.float64, A.device)
+    Q = empty_colmajor(N, M, torch.float64, A.device) if want_q else None
+    st = lib.pylom_tsqr(_dptr(A), N, M, _ld(A), xtype, leaf_rows, _dptr(R), _ld(R),
+                        _dptr(Q), _ld(Q) if Q is not None else N, prec, _dptr(ws), ws.numel(),
+                        _stream(stream))
+    _raise(st, "pylom_tsqr")
+    if check:
+        st, _, _ = workspace_status(ws, stream)
+        _raise(st, "pylom_tsqr (device)")
+    return R, Q
+
+
+def svd_small(R, max_sweeps=60, stream=None, check=True):
+    """SVD of a small square FP64 matrix (Eq. svdqr2): returns (U, S, VT, sweeps)."""
+    torch = _torch()
+    lib = load_library()
+    R = _colmajor(R.to(torch.float64))
+    M = R.shape[0]
+    if R.shape[1] != M:
+        raise ValueError("svd_small expects a square matrix")
+    need = lib.pylom_svd_small_workspace_size(M)
+    ws = torch.empty(max(need, 512), dtype=torch.uint8, device=R.device)
+    U = empty_colmajor(M, M, torch.float64, R.device)
+    VT = empty_colmajor(M, M, torch.float64, R.device)
+    S = torch.empty(M, dtype=torch.float64, device=R.device)
+    st = lib.pylom_svd_small(_dptr(R), M, _ld(R), _dptr(U), _ld(U), _dptr(S), _dptr(VT),
+                             _ld(VT), int(max_sweeps), _dptr(ws), ws.numel(), _stream(stream))
+    _raise(st, "pylom_svd_small")
+    sweeps = -1
+    if check:
+        st, _, sweeps = workspace_status(ws, stream)
+        _raise(st, "pylom_svd_small (device)")
+    return U, S, VT, sweeps
+
+
+def matmul(A, B, transA=False, stream=None):
+    """Alg. 4's local product C = op(A) B (FP64)."""
+    torch = _torch()
+    lib = load_library()
+    A = _colmajor(A.to(torch.float64))
+    B = _colmajor(B.to(torch.float64))
+    m, k = (A.shape[1], A.shape[0]) if transA else A.shape
+    if B.shape[0] != k:
+        raise ValueError("inner dimensions differ")
+    n = B.shape[1]
+    need = lib.pylom_matmul_workspace_size(m, n, k)
+    ws = torch.empty(max(need, 256), dtype=torch.uint8, device=A.device)
+    C = empty_colmajor(m, n, torch.float64, A.device)
+    st = lib.pylom_matmul(int(bool(transA)), _dptr(A), _dptr(B), _dptr(C), m, n, k, _ld(A),
+                          _ld(B), _ld(C), _dptr(ws), ws.numel(), _stream(stream))
+    _raise(st, "pylom_matmul")
+    return C

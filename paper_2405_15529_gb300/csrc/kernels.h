@@ -1,0 +1,68 @@
+// kernels.h -- internal launchers behind the C ABI (host side).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace pylom {
+
+// Householder panel width of the FP64 leaf QR (two 8-row DMMA tiles).
+constexpr int kNB = 16;
+
+// Device pointers of one TSQR (+ modes) problem, carved from a workspace.
+struct TsqrState {
+  WsHeader* hdr;
+  int64_t N, M, P;          // rows, columns, leaves
+  int64_t npan;             // panels per leaf = ceil(M / kNB)
+  double* Y;                // N x M working matrix -> reflectors (ld N)
+  double* tau;              // P x M leaf reflector scalars
+  double* T;                // P x npan x kNB x kNB block-reflector factors
+  double* Rs;               // P x M x M: leaf R, then merged R (left) or node reflectors (right)
+  double* tau_tree;         // P x M tree-node reflector scalars (indexed by right child)
+  unsigned* arrive;         // P arrival counters of the tree merges
+  double* B;                // P x M x rmax down-pass blocks (nullable if no modes)
+  int64_t rmax;
+};
+
+struct SvdState {
+  WsHeader* hdr;
+  int64_t M, Mp;            // size, padded to even
+  double* A;                // M x Mp working columns
+  double* V;                // Mp x Mp accumulated rotations
+};
+
+size_t tsqr_state_bytes(int64_t N, int64_t M, int64_t P, int64_t rmax);
+void tsqr_state_carve(TsqrState& s, char* base, int64_t N, int64_t M, int64_t P, int64_t rmax);
+size_t svd_state_bytes(int64_t M);
+void svd_state_carve(SvdState& s, char* base, int64_t M);
+
+// Leaf QR of every row block (with fused mean/weight prologue) and the
+// last-arriver tree reduction; the root R ends in Rs[0].
+cudaError_t launch_tsqr_fp64(const TsqrState& s, const void* X, int64_t ldx, int xtype,
+                             const double* w, int remove_mean, double* mean, cudaStream_t st);
+
+// Copy the root R (upper triangle) into an M x M matrix with zeros below.
+cudaError_t launch_copy_root_r(const TsqrState& s, double* R, int64_t ldr, cudaStream_t st);
+
+// Parallel one-sided Jacobi + sort/sign/truncate.  Input R (M x M, ldr).
+// Writes U (M x M, ldu), S, VT (ldvt) and, if energy/r_max given, hdr->r.
+cudaError_t launch_svd_fp64(const SvdState& s, const double* R, int64_t ldr, double* U, int64_t ldu,
+                            double* S, double* VT, int64_t ldvt, int max_sweeps, double energy,
+                            int64_t r_max, cudaStream_t st);
+
+// Down pass through the tree (B_root = first r columns of Ur, or identity when
+// Ur == nullptr) and the per-leaf modes product U = Q [B_leaf; 0].  The number
+// of columns is r_fixed if >= 0, else read from hdr->r on the device.
+// `mid` (nullable) is recorded between the down pass and the leaf modes kernel.
+cudaError_t launch_modes_fp64(const TsqrState& s, const double* Ur, int64_t ldur, int64_t r_fixed,
+                              const double* w, int physical, double* U, int64_t ldu,
+                              int64_t* r_out, cudaStream_t st, cudaEvent_t mid = nullptr);
+
+// C = op(A) B in binary64 on the FP64 tensor pipe.
+size_t matmul_ws_bytes(int64_t m, int64_t n, int64_t k);
+cudaError_t launch_matmul_fp64(int transA, const double* A, const double* B, double* C, int64_t m,
+                               int64_t n, int64_t k, int64_t lda, int64_t ldb, int64_t ldc,
+                               double* ws, cudaStream_t st);
+
+}  // namespace pylom

@@ -1,0 +1,543 @@
+// tsqr_fp64.cu -- binary64 TSQR (Alg. 1 of pyLOM, arXiv 2405.15529) on one
+// GB300, plus the top-down pass and the modes product U = Q U_r (Eq. svdqr3).
+//
+// Layout (all column-major):
+//   Y   N x M   the weighted, mean-removed snapshot matrix, overwritten leaf
+//               by leaf with Householder vectors (unit diagonal implicit).
+//   T   per leaf and panel: the kNB x kNB upper-triangular factor of the
+//               compact-WY form Q_panel = I - V T V^T.
+//   Rs  per leaf an M x M slot: the leaf R, then either the merged R (left
+//               child, the receiver of Alg. 1) or the merge's reflectors
+//               (right child, the sender).
+//
+// The paper's processes become row blocks ("leaves", one thread block
+// each) and its binary-tree reduction becomes last-arriver merges across
+// thread blocks: at every level the block that finishes second merges the
+// pair (left child's R on top, as the receiver keeps its own R in the upper
+// half of C in Alg. 1), so no block ever waits on another.
+#include "kernels.h"
+
+namespace pylom {
+
+constexpr int kLeafThreads = 256;
+constexpr int kCW = 256;   // column chunk of a block-reflector application
+constexpr int kTPW = 4;    // 8-column tiles per warp in W = V^T C
+
+// Shared-memory plan of the leaf / modes kernels (doubles).
+constexpr int kSmT = kNB * kNB;
+constexpr int kSmRed = kNB * 32;
+constexpr int kSmOut = 32;
+constexpr int kSmW = kNB * kCW;
+constexpr size_t kLeafSmemBytes = sizeof(double) * (kSmT + kSmRed + kSmOut + 2 * kSmW);
+
+// Entry (i, p) of the panel's reflector matrix V (panel starts at column k,
+// nbk reflectors, h rows): zero above the diagonal, one on it, stored below.
+__device__ __forceinline__ double vval(const double* A, int64_t lda, int64_t k, int nbk,
+                                       int64_t h, int64_t i, int p) {
+  if (p >= nbk || i >= h) return 0.0;
+  const int64_t d = k + p;
+  if (i < d) return 0.0;
+  if (i == d) return 1.0;
+  return A[i + d * lda];
+}
+
+// C[k:h, 0:ncols] := (I - V op(T) V^T) C[k:h, 0:ncols] with op(T) = T^T
+// (TRANS: applies Q_panel^T, the factorisation's trailing update) or T
+// (applies Q_panel, the modes product).  The two contractions W = V^T C and
+// C -= V W' run on the FP64 tensor pipe (mma.sync m8n8k4); W is reduced over
+// K slices in a fixed order, so results are bitwise repeatable.
+template <bool TRANS>
+__device__ void apply_block_reflector(const double* A, int64_t lda, int64_t k, int nbk, int64_t h,
+                                      double* C, int64_t ldc, int ncols, const double* sT,
+                                      double* sW, double* sWp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int64_t L = h - k;
+  const int64_t nsteps = (L + 3) / 4;
+  for (int c0 = 0; c0 < ncols; c0 += kCW) {
+    const int wc = min(kCW, ncols - c0);
+    const int NT = (wc + 7) / 8;
+    const int G = (NT + kTPW - 1) / kTPW;
+    const int S = (G >= nwarps) ? 1 : nwarps / G;
+    const int WcP = G * kTPW * 8;
+    // phase 1: partial W = V^T C over S slices of the rows
+    for (int u = warp; u < G * S; u += nwarps) {
+      const int gi = u % G, si = u / G;
+      const int64_t sb = (nsteps * si) / S, se = (nsteps * (si + 1)) / S;
+      double acc[2][kTPW][2];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int tt = 0; tt < kTPW; ++tt) acc[mt][tt][0] = acc[mt][tt][1] = 0.0;
+      for (int64_t stp = sb; stp < se; ++stp) {
+        const int64_t row = k + stp * 4 + t;
+        const double a0 = vval(A, lda, k, nbk, h, row, g);
+        const double a1 = vval(A, lda, k, nbk, h, row, 8 + g);
+        const bool rok = row < h;
+#pragma unroll
+        for (int tt = 0; tt < kTPW; ++tt) {
+          const int col = (gi * kTPW + tt) * 8 + g;
+          const double b = (rok && col < wc) ? C[row + (int64_t)(c0 + col) * ldc] : 0.0;
+          dmma884(acc[0][tt][0], acc[0][tt][1], a0, b);
+          dmma884(acc[1][tt][0], acc[1][tt][1], a1, b);
+        }
+      }
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int tt = 0; tt < kTPW; ++tt) {
+          const int p = mt * 8 + g;
+          const int col = (gi * kTPW + tt) * 8 + 2 * t;
+          sWp[(si * kNB + p) * WcP + col] = acc[mt][tt][0];
+          sWp[(si * kNB + p) * WcP + col + 1] = acc[mt][tt][1];
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kNB * WcP; idx += blockDim.x) {
+      double s = 0.0;
+      for (int si = 0; si < S; ++si) s += sWp[si * kNB * WcP + idx];
+      sW[idx] = s;
+    }
+    __syncthreads();
+    // phase 2: sWp = -op(T) W
+    for (int idx = threadIdx.x; idx < kNB * WcP; idx += blockDim.x) {
+      const int p = idx / WcP, col = idx - p * WcP;
+      double s = 0.0;
+      if (TRANS) {
+        for (int q = 0; q <= p; ++q) s += sT[q * kNB + p] * sW[q * WcP + col];
+      } else {
+        for (int q = p; q < kNB; ++q) s += sT[p * kNB + q] * sW[q * WcP + col];
+      }
+      sWp[idx] = -s;
+    }
+    __syncthreads();
+    // phase 3: C += V (-W')
+    const int64_t nrt = (L + 7) / 8;
+    for (int64_t rt = warp; rt < nrt; rt += nwarps) {
+      const int64_t i0 = k + rt * 8;
+      double a[4];
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) a[ks] = vval(A, lda, k, nbk, h, i0 + g, ks * 4 + t);
+      const int64_t row = i0 + g;
+      const bool rok = row < h;
+      for (int ct = 0; ct < NT; ++ct) {
+        const int col = ct * 8 + 2 * t;
+        double* cp = C + row + (int64_t)(c0 + col) * ldc;
+        double d0 = (rok && col < wc) ? cp[0] : 0.0;
+        double d1 = (rok && col + 1 < wc) ? cp[ldc] : 0.0;
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks)
+          dmma884(d0, d1, a[ks], sWp[(ks * 4 + t) * WcP + ct * 8 + g]);
+        if (rok && col < wc) cp[0] = d0;
+        if (rok && col + 1 < wc) cp[ldc] = d1;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Householder factorisation of the panel A[k:h, k:k+nbk] (Eq. svdqr1 on a
+// row block), textbook convention beta = -sign(alpha)|x|, sign(0) = +1.
+// Builds T (row-major kNB x kNB, upper) by the forward recurrence
+// T[0:j, j] = -tau_j T[0:j, 0:j] (V[:, 0:j]^T v_j).  Scalar FP64: each column
+// is one pass that scales v_j and forms its dot products with the panel,
+// then one pass that updates the panel (and the next column's norm).
+__device__ void panel_factor(double* A, int64_t lda, int64_t k, int nbk, int64_t h, double* tau_out,
+                             double* sT, double* sred, double* sout) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  double xx;
+  {
+    double v[1] = {0.0};
+    for (int64_t i = k + 1 + tid; i < h; i += nthr) {
+      const double a = A[i + k * lda];
+      v[0] += a * a;
+    }
+    block_sum<1>(v, sred, sout);
+    xx = sout[0];
+  }
+  for (int jj = 0; jj < nbk; ++jj) {
+    const int64_t j = k + jj;
+    const double alpha = A[j + j * lda];
+    double tau_j = 0.0, beta = alpha, scale = 0.0;
+    if (xx != 0.0) {
+      const double nrm = sqrt(alpha * alpha + xx);
+      beta = (alpha >= 0.0) ? -nrm : nrm;
+      tau_j = (beta - alpha) / beta;
+      scale = 1.0 / (alpha - beta);
+    }
+    double acc[kNB];
+#pragma unroll
+    for (int c = 0; c < kNB; ++c) acc[c] = 0.0;
+    for (int64_t i = j + tid; i < h; i += nthr) {
+      double v = 1.0;
+      if (i != j) {
+        v = A[i + j * lda] * scale;
+        A[i + j * lda] = v;
+      }
+#pragma unroll
+      for (int c = 0; c < kNB; ++c)
+        if (c < nbk && c != jj) acc[c] += v * A[i + (k + c) * lda];
+    }
+    block_sum<kNB>(acc, sred, sout);
+    if (tid == 0) {
+      A[j + j * lda] = beta;
+      tau_out[jj] = tau_j;
+      for (int p = 0; p < jj; ++p) {
+        double s = 0.0;
+        for (int q = p; q < jj; ++q) s += sT[p * kNB + q] * sout[q];
+        sT[p * kNB + jj] = -tau_j * s;
+      }
+      sT[jj * kNB + jj] = tau_j;
+    }
+    double nx[1] = {0.0};
+    if (jj + 1 < nbk) {
+      for (int64_t i = j + tid; i < h; i += nthr) {
+        const double v = (i == j) ? 1.0 : A[i + j * lda];
+#pragma unroll
+        for (int c = 0; c < kNB; ++c) {
+          if (c > jj && c < nbk) {
+            const double a = A[i + (k + c) * lda] - tau_j * sout[c] * v;
+            A[i + (k + c) * lda] = a;
+            if (c == jj + 1 && i > j + 1) nx[0] += a * a;
+          }
+        }
+      }
+    }
+    block_sum<1>(nx, sred, sout);
+    xx = sout[0];
+  }
+}
+
+// QR of the stacked pair [Rt; Rb] of two upper-triangular M x M factors
+// (the buffer C of Alg. 1, receiver's R on top).  Reflector c touches only
+// row c of the top and rows 0..c of the bottom, so it is stored in column c
+// of Rb (rows 0..c) and the merged R overwrites Rt.  Loads bypass L1: the
+// partner's R was written by another block.
+__device__ void tree_merge(double* Rt, double* Rb, double* tau, int64_t M, double* su,
+                           double* sred) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
+  for (int64_t c = 0; c < M; ++c) {
+    if (warp == 0) {
+      double xx = 0.0;
+      for (int64_t i = lane; i <= c; i += 32) {
+        const double v = ldcg(Rb + i + c * M);
+        xx += v * v;
+      }
+      xx = warp_sum(xx);
+      if (lane == 0) {
+        const double alpha = ldcg(Rt + c + c * M);
+        double tc = 0.0, beta = alpha, scale = 0.0;
+        if (xx != 0.0) {
+          const double nrm = sqrt(alpha * alpha + xx);
+          beta = (alpha >= 0.0) ? -nrm : nrm;
+          tc = (beta - alpha) / beta;
+          scale = 1.0 / (alpha - beta);
+        }
+        sred[0] = tc;
+        sred[1] = scale;
+        Rt[c + c * M] = beta;
+        tau[c] = tc;
+      }
+    }
+    __syncthreads();
+    const double tc = sred[0], scale = sred[1];
+    for (int64_t i = tid; i <= c; i += nthr) {
+      const double u = ldcg(Rb + i + c * M) * scale;
+      Rb[i + c * M] = u;
+      su[i] = u;
+    }
+    __syncthreads();
+    if (tc != 0.0) {
+      for (int64_t cc = c + 1 + warp; cc < M; cc += nwarps) {
+        double s = 0.0;
+        for (int64_t i = lane; i <= c; i += 32) s += su[i] * ldcg(Rb + i + cc * M);
+        s = (warp_sum(s) + ldcg(Rt + c + cc * M)) * tc;
+        for (int64_t i = lane; i <= c; i += 32) Rb[i + cc * M] = ldcg(Rb + i + cc * M) - s * su[i];
+        if (lane == 0) Rt[c + cc * M] = ldcg(Rt + c + cc * M) - s;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+struct LeafArgs {
+  TsqrState s;
+  const void* X;
+  int64_t ldx;
+  int xtype;
+  const double* w;
+  int remove_mean;
+  double* mean;
+};
+
+template <typename TX>
+__device__ void leaf_prologue(const LeafArgs& a, double* A, int64_t lda, int64_t r0, int64_t h) {
+  const TX* X = (const TX*)a.X;
+  const int64_t M = a.s.M;
+  int bad = 0;
+  for (int64_t i = threadIdx.x; i < h; i += blockDim.x) {
+    const int64_t n = r0 + i;
+    double xbar = 0.0;
+    if (a.remove_mean) {
+      double sum = 0.0;
+      for (int64_t m = 0; m < M; ++m) sum += (double)X[n + m * a.ldx];
+      xbar = sum / (double)M;
+    }
+    if (a.mean) a.mean[n] = xbar;
+    double sw = 1.0;
+    if (a.w) {
+      const double wn = a.w[n];
+      if (!(wn > 0.0) || !isfinite(wn)) bad = 1;
+      sw = sqrt(wn);
+    }
+    for (int64_t m = 0; m < M; ++m) {
+      const double x = (double)X[n + m * a.ldx];
+      if (!isfinite(x)) bad = 1;
+      A[i + m * lda] = sw * (x - xbar);
+    }
+  }
+  if (bad) raise_status(a.s.hdr, PYLOM_ERR_NONFINITE);
+}
+
+__global__ void __launch_bounds__(kLeafThreads) leaf_qr_kernel(LeafArgs a) {
+  extern __shared__ double smem[];
+  double* sT = smem;
+  double* sred = sT + kSmT;
+  double* sout = sred + kSmRed;
+  double* sW = sout + kSmOut;
+  double* sWp = sW + kSmW;
+  const TsqrState& s = a.s;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int64_t leaf = blockIdx.x;
+  const int64_t r0 = leaf_begin(leaf, s.N, s.P);
+  const int64_t h = leaf_begin(leaf + 1, s.N, s.P) - r0;
+  const int64_t M = s.M, lda = s.N;
+  double* A = s.Y + r0;
+
+  if (a.xtype == PYLOM_F32)
+    leaf_prologue<float>(a, A, lda, r0, h);
+  else
+    leaf_prologue<double>(a, A, lda, r0, h);
+  __syncthreads();
+
+  for (int64_t k = 0; k < M; k += kNB) {
+    const int nbk = (int)((M - k) < kNB ? (M - k) : kNB);
+    for (int idx = tid; idx < kSmT; idx += nthr) sT[idx] = 0.0;
+    __syncthreads();
+    panel_factor(A, lda, k, nbk, h, s.tau + leaf * M + k, sT, sred, sout);
+    __syncthreads();
+    double* Tg = s.T + (leaf * s.npan + k / kNB) * kSmT;
+    for (int idx = tid; idx < kSmT; idx += nthr) Tg[idx] = sT[idx];
+    if (k + nbk < M)
+      apply_block_reflector<true>(A, lda, k, nbk, h, A + (k + nbk) * lda, lda, (int)(M - k - nbk),
+                                  sT, sW, sWp);
+    __syncthreads();
+  }
+
+  // leaf R into its slot (zeros below the diagonal)
+  double* Rl = s.Rs + leaf * M * M;
+  for (int64_t idx = tid; idx < M * M; idx += nthr) {
+    const int64_t i = idx % M, j = idx / M;
+    Rl[idx] = (i <= j) ? A[i + j * lda] : 0.0;
+  }
+  __threadfence();
+  __syncthreads();
+
+  // Binary tree of Alg. 1: at step 2^l the subtree rooted at `node` pairs
+  // with node ^ 2^l; a missing partner (>= P) passes R up unchanged.
+  __shared__ unsigned s_prev;
+  int64_t node = leaf;
+  for (int64_t step = 1; step < s.P; step <<= 1) {
+    int64_t left, right;
+    if (node & step) {
+      left = node - step;
+      right = node;
+    } else {
+      right = node + step;
+      if (right >= s.P) continue;
+      left = node;
+    }
+    if (tid == 0) s_prev = atomicAdd(&s.arrive[right], 1u);
+    __syncthreads();
+    if (s_prev == 0) return;  // first to arrive: the partner merges
+    __threadfence();
+    tree_merge(s.Rs + left * M * M, s.Rs + right * M * M, s.tau_tree + right * M, M, sW, sred);
+    __threadfence();
+    __syncthreads();
+    node = left;
+  }
+}
+
+// Top-down pass (the broadcast loop of Alg. 1): at a merge of `left` and
+// `right`, [B_left; B_right] = Q_node [B_left; 0], applying the node's
+// reflectors in reverse order.  One warp per column of B.
+__global__ void __launch_bounds__(256) down_pass_kernel(TsqrState s, int64_t step, int64_t r_fixed) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int64_t left = (int64_t)blockIdx.x * 2 * step, right = left + step;
+  if (right >= s.P) return;
+  const int64_t r = (r_fixed >= 0) ? r_fixed : s.hdr->r;
+  const int64_t col = (int64_t)blockIdx.y * nwarps + warp;
+  if (col >= r) return;
+  const int64_t M = s.M;
+  double* Bt = s.B + left * M * s.rmax + col * M;
+  double* Bb = s.B + right * M * s.rmax + col * M;
+  const double* U = s.Rs + right * M * M;
+  const double* tau = s.tau_tree + right * M;
+  for (int64_t i = lane; i < M; i += 32) Bb[i] = 0.0;
+  __syncwarp();
+  for (int64_t c = M - 1; c >= 0; --c) {
+    const double tc = tau[c];
+    if (tc == 0.0) continue;
+    double acc = 0.0;
+    for (int64_t i = lane; i <= c; i += 32) acc += U[i + c * M] * Bb[i];
+    acc = (warp_sum(acc) + Bt[c]) * tc;
+    __syncwarp();
+    if (lane == 0) Bt[c] -= acc;
+    for (int64_t i = lane; i <= c; i += 32) Bb[i] -= acc * U[i + c * M];
+    __syncwarp();
+  }
+}
+
+// B_root = first r columns of Ur (or the identity when Ur is null).
+__global__ void init_root_kernel(TsqrState s, const double* Ur, int64_t ldur, int64_t r_fixed) {
+  const int64_t r = (r_fixed >= 0) ? r_fixed : s.hdr->r;
+  const int64_t M = s.M;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < M * r;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % M, c = idx / M;
+    s.B[idx] = Ur ? Ur[i + c * ldur] : (i == c ? 1.0 : 0.0);
+  }
+}
+
+// Per leaf: U_leaf = Q_leaf [B_leaf; 0], the panels applied last to first
+// (Q_leaf = Q_panel0 Q_panel1 ...), then Phi = U / sqrt(w) if asked.
+__global__ void __launch_bounds__(kLeafThreads) modes_kernel(TsqrState s, int64_t r_fixed,
+                                                            const double* w, int physical,
+                                                            double* U, int64_t ldu,
+                                                            int64_t* r_out) {
+  extern __shared__ double smem[];
+  double* sT = smem;
+  double* sW = sT + kSmT + kSmRed + kSmOut;
+  double* sWp = sW + kSmW;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int64_t leaf = blockIdx.x;
+  const int64_t r0 = leaf_begin(leaf, s.N, s.P);
+  const int64_t h = leaf_begin(leaf + 1, s.N, s.P) - r0;
+  const int64_t M = s.M;
+  const int64_t r = (r_fixed >= 0) ? r_fixed : s.hdr->r;
+  if (leaf == 0 && tid == 0 && r_out) *r_out = r;
+  double* C = U + r0;
+  const double* Bl = s.B + leaf * M * s.rmax;
+  for (int64_t c = 0; c < r; ++c)
+    for (int64_t i = tid; i < h; i += nthr) C[i + c * ldu] = (i < M) ? Bl[i + c * M] : 0.0;
+  __syncthreads();
+  const double* A = s.Y + r0;
+  for (int64_t pan = s.npan - 1; pan >= 0; --pan) {
+    const int64_t k = pan * kNB;
+    const int nbk = (int)((M - k) < kNB ? (M - k) : kNB);
+    const double* Tg = s.T + (leaf * s.npan + pan) * kSmT;
+    for (int idx = tid; idx < kSmT; idx += nthr) sT[idx] = Tg[idx];
+    __syncthreads();
+    apply_block_reflector<false>(A, s.N, k, nbk, h, C, ldu, (int)r, sT, sW, sWp);
+    __syncthreads();
+  }
+  if (physical && w) {
+    for (int64_t i = tid; i < h; i += nthr) {
+      const double iw = 1.0 / sqrt(w[r0 + i]);
+      for (int64_t c = 0; c < r; ++c) C[i + c * ldu] *= iw;
+    }
+  }
+}
+
+__global__ void copy_root_kernel(TsqrState s, double* R, int64_t ldr) {
+  const int64_t M = s.M;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < M * M;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % M, j = idx / M;
+    R[i + j * ldr] = (i <= j) ? s.Rs[idx] : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+size_t tsqr_state_bytes(int64_t N, int64_t M, int64_t P, int64_t rmax) {
+  const int64_t npan = (M + kNB - 1) / kNB;
+  size_t b = 0;
+  b += align256(sizeof(double) * (size_t)N * M);
+  b += align256(sizeof(double) * (size_t)P * M);
+  b += align256(sizeof(double) * (size_t)P * npan * kNB * kNB);
+  b += align256(sizeof(double) * (size_t)P * M * M);
+  b += align256(sizeof(double) * (size_t)P * M);
+  b += align256(sizeof(unsigned) * (size_t)P);
+  b += align256(sizeof(double) * (size_t)P * M * rmax);
+  return b;
+}
+
+void tsqr_state_carve(TsqrState& s, char* base, int64_t N, int64_t M, int64_t P, int64_t rmax) {
+  s.N = N;
+  s.M = M;
+  s.P = P;
+  s.npan = (M + kNB - 1) / kNB;
+  s.rmax = rmax;
+  char* p = base;
+  s.Y = (double*)p;        p += align256(sizeof(double) * (size_t)N * M);
+  s.tau = (double*)p;      p += align256(sizeof(double) * (size_t)P * M);
+  s.T = (double*)p;        p += align256(sizeof(double) * (size_t)P * s.npan * kNB * kNB);
+  s.Rs = (double*)p;       p += align256(sizeof(double) * (size_t)P * M * M);
+  s.tau_tree = (double*)p; p += align256(sizeof(double) * (size_t)P * M);
+  s.arrive = (unsigned*)p; p += align256(sizeof(unsigned) * (size_t)P);
+  s.B = rmax > 0 ? (double*)p : nullptr;
+}
+
+cudaError_t launch_tsqr_fp64(const TsqrState& s, const void* X, int64_t ldx, int xtype,
+                             const double* w, int remove_mean, double* mean, cudaStream_t st) {
+  cudaError_t e;
+  static bool attr_set = false;
+  if (!attr_set) {
+    e = cudaFuncSetAttribute(leaf_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kLeafSmemBytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(modes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kLeafSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  LeafArgs a{s, X, ldx, xtype, w, remove_mean, mean};
+  leaf_qr_kernel<<<(unsigned)s.P, kLeafThreads, kLeafSmemBytes, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_root_r(const TsqrState& s, double* R, int64_t ldr, cudaStream_t st) {
+  copy_root_kernel<<<64, 256, 0, st>>>(s, R, ldr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_modes_fp64(const TsqrState& s, const double* Ur, int64_t ldur, int64_t r_fixed,
+                              const double* w, int physical, double* U, int64_t ldu,
+                              int64_t* r_out, cudaStream_t st, cudaEvent_t mid) {
+  init_root_kernel<<<64, 256, 0, st>>>(s, Ur, ldur, r_fixed);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int64_t top = 1;
+  while (top * 2 < s.P) top *= 2;
+  const unsigned ycols = (unsigned)((s.rmax + 7) / 8);
+  for (int64_t step = (s.P > 1 ? top : 0); step >= 1; step >>= 1) {
+    const int64_t merges = (s.P - step + 2 * step - 1) / (2 * step);
+    dim3 grid((unsigned)merges, ycols);
+    down_pass_kernel<<<grid, 256, 0, st>>>(s, step, r_fixed);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (mid) {
+    e = cudaEventRecord(mid, st);
+    if (e != cudaSuccess) return e;
+  }
+  modes_kernel<<<(unsigned)s.P, kLeafThreads, kLeafSmemBytes, st>>>(s, r_fixed, w, physical, U, ldu,
+                                                                    r_out);
+  return cudaGetLastError();
+}
+
+}  // namespace pylom
