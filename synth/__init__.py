@@ -143,17 +143,24 @@ def known_spectrum(N: int, M: int, s=None, weights: bool = True, seeds=(2, 3, 4)
 def known_spectrum_torch(N: int, M: int, device, s=None, weights: bool = True, seeds=(2, 3, 4),
                          dtype=None):
     """Device-side :func:`known_spectrum` for large N.  Returns (XT, w, s) with
-    XT of shape (M, N) (so XT.T is the column-major N x M matrix)."""
+    XT of shape (M, N) (so XT.T is the column-major N x M matrix).  Q1 is a
+    different seeded orthonormal factor than the host version's (same
+    distribution up to the orthonormalisation route)."""
     import torch
     dtype = dtype or torch.float64
     if s is None:
         s = spectrum(M)
     gen = torch.Generator(device=device)
     gen.manual_seed(seeds[0])
-    G = torch.randn((N, M), dtype=torch.float64, device=device, generator=gen)
-    Q1, R1 = torch.linalg.qr(G)
-    Q1 *= torch.sign(torch.diagonal(R1))[None, :]
-    del G, R1
+    Q1 = torch.randn((N, M), dtype=torch.float64, device=device, generator=gen)
+    # orthonormalise the Gaussian by two Cholesky-QR passes: Gram matrix on
+    # the device, its M x M Cholesky factor inverted on the host (no device
+    # linear-algebra library needed), one product per pass
+    for _ in range(2):
+        gram = (Q1.T @ Q1).cpu()
+        L = torch.linalg.cholesky(gram)
+        Linv_t = torch.linalg.inv(L).T.contiguous().to(device)
+        Q1 = Q1 @ Linv_t
     Q2 = torch.tensor(haar_orthogonal(M, seeds[1]), dtype=torch.float64, device=device)
     st = torch.tensor(s, dtype=torch.float64, device=device)
     Y = (Q1 * st[None, :]) @ Q2.T
