@@ -165,6 +165,26 @@ pylom_status pylom_matmul(int transA, const double* A, const double* B, double* 
                           void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
+ * pylom_svd_small_noalloc -- the SVD of pylom_svd_small for callers that
+ * cannot give the library device memory (no counterpart in the paper).
+ * A host code that owns all device buffers through its own allocator, or a
+ * loop that may not allocate once running, passes only R and the outputs;
+ * the scratch is a fixed array inside the library (about 1 MiB per device
+ * that loads it, held until the process exits).
+ *  R, U, S, VT, ldr, ldu, ldvt, max_sweeps   as pylom_svd_small.
+ *  M      1 <= M <= 256; larger M returns PYLOM_ERR_SHAPE (use
+ *         pylom_svd_small with a workspace).
+ *  info   device int[2] or NULL: receives the device status (pylom_status)
+ *         and the Jacobi sweeps used, stream-ordered after the SVD.
+ * The first call on a device looks up the array's device address (once per
+ * device); make it before any stream capture.  All calls share the array:
+ * calls that may overlap on the GPU race and must be ordered on one stream.
+ * ------------------------------------------------------------------------ */
+pylom_status pylom_svd_small_noalloc(const double* R, int64_t M, int64_t ldr, double* U,
+                                     int64_t ldu, double* S, double* VT, int64_t ldvt,
+                                     int max_sweeps, int* info, void* stream);
+
+/* ------------------------------------------------------------------------
  * Phase profiler (measurement support; no counterpart in the paper).
  * Between begin and end, each of the next max_calls pylom_pod calls records
  * CUDA events on its own stream at the boundaries of its phases:

@@ -35,7 +35,7 @@ EXPORTS = (
     "pylom_pod_workspace_size", "pylom_pod", "pylom_tsqr_workspace_size", "pylom_tsqr",
     "pylom_svd_small_workspace_size", "pylom_svd_small", "pylom_matmul_workspace_size",
     "pylom_matmul", "pylom_profile_begin", "pylom_profile_end",
-    "pylom_probe_scratch_bytes", "pylom_probe_fp64_peak",
+    "pylom_probe_scratch_bytes", "pylom_probe_fp64_peak", "pylom_svd_small_noalloc",
 )
 PROFILE_PHASES = ("leaf_qr_tree", "svd_small", "down_pass", "modes")
 
@@ -90,6 +90,8 @@ def load_library(path: str = LIB_PATH):
     lib.pylom_profile_begin.argtypes = [_int]
     lib.pylom_profile_end.restype = _int
     lib.pylom_profile_end.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_int)]
+    lib.pylom_svd_small_noalloc.restype = _int
+    lib.pylom_svd_small_noalloc.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _int, _vp, _vp]
     lib.pylom_probe_scratch_bytes.restype = _sz
     lib.pylom_probe_fp64_peak.restype = _int
     lib.pylom_probe_fp64_peak.argtypes = [_int, _vp, ctypes.POINTER(ctypes.c_double), _vp]
@@ -287,6 +289,28 @@ def svd_small(R, max_sweeps=60, stream=None, check=True):
         st, _, sweeps = workspace_status(ws, stream)
         _raise(st, "pylom_svd_small (device)")
     return U, S, VT, sweeps
+
+
+def svd_small_noalloc(R, max_sweeps=60, stream=None):
+    """pylom_svd_small_noalloc: the small SVD with the library's fixed scratch
+    (M <= 256; no workspace).  Returns (U, S, VT, status, sweeps) after
+    synchronising the stream."""
+    torch = _torch()
+    lib = load_library()
+    R = _colmajor(R.to(torch.float64))
+    M = R.shape[0]
+    if R.shape[1] != M:
+        raise ValueError("svd_small_noalloc expects a square matrix")
+    U = empty_colmajor(M, M, torch.float64, R.device)
+    VT = empty_colmajor(M, M, torch.float64, R.device)
+    S = torch.empty(M, dtype=torch.float64, device=R.device)
+    info = torch.full((2,), -1, dtype=torch.int32, device=R.device)
+    st = lib.pylom_svd_small_noalloc(_dptr(R), M, _ld(R), _dptr(U), _ld(U), _dptr(S), _dptr(VT),
+                                     _ld(VT), int(max_sweeps), _dptr(info), _stream(stream))
+    _raise(st, "pylom_svd_small_noalloc")
+    (stream if stream is not None else torch.cuda.current_stream()).synchronize()
+    inf = info.cpu().tolist()
+    return U, S, VT, int(inf[0]), int(inf[1])
 
 
 def matmul(A, B, transA=False, stream=None):

@@ -65,6 +65,13 @@ bool aligned256(const void* p) { return ((uintptr_t)p & 255u) == 0; }
 
 }  // namespace
 
+void pylom::set_error_message(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
 extern "C" const char* pylom_version(void) { return "pylom-gb300 0.1.0 (sm_103a, FP64 TSQR-SVD)"; }
 
 extern "C" const char* pylom_last_error(void) { return g_err; }

@@ -59,6 +59,9 @@ cudaError_t launch_modes_fp64(const TsqrState& s, const double* Ur, int64_t ldur
                               const double* w, int physical, double* U, int64_t ldu,
                               int64_t* r_out, cudaStream_t st, cudaEvent_t mid = nullptr);
 
+// Records a message for pylom_last_error() on the calling host thread.
+void set_error_message(const char* fmt, ...);
+
 // C = op(A) B in binary64 on the FP64 tensor pipe.
 size_t matmul_ws_bytes(int64_t m, int64_t n, int64_t k);
 cudaError_t launch_matmul_fp64(int transA, const double* A, const double* B, double* C, int64_t m,
