@@ -111,7 +111,7 @@ __device__ __forceinline__ bool grid_barrier(WsHeader* h, unsigned nblocks) {
             break;
           }
           if (read_status(h) == PYLOM_ERR_TIMEOUT) { ok = 0; break; }
-          __nanosleep(64);
+          __nanosleep(20);
         }
       }
       __threadfence();

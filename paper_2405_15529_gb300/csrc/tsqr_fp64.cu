@@ -30,29 +30,58 @@ constexpr int kSmOut = 32;
 constexpr int kSmW = kNB * kCW;
 constexpr size_t kLeafSmemBytes = sizeof(double) * (kSmT + kSmRed + kSmOut + 2 * kSmW);
 
-// Entry (i, p) of the panel's reflector matrix V (panel starts at column k,
-// nbk reflectors, h rows): zero above the diagonal, one on it, stored below.
-__device__ __forceinline__ double vval(const double* A, int64_t lda, int64_t k, int nbk,
-                                       int64_t h, int64_t i, int p) {
-  if (p >= nbk || i >= h) return 0.0;
-  const int64_t d = k + p;
-  if (i < d) return 0.0;
-  if (i == d) return 1.0;
-  return A[i + d * lda];
+// Entry (i, p) of a leaf panel's reflector matrix V (panel starts at
+// column k, nbk reflectors, h rows): zero above the diagonal, one on it,
+// stored below.
+struct LeafV {
+  const double* A;
+  int64_t lda, k, h;
+  int nbk;
+  __device__ __forceinline__ double operator()(int64_t i, int p) const {
+    if (p >= nbk || i >= h) return 0.0;
+    const int64_t d = k + p;
+    if (i < d) return 0.0;
+    if (i == d) return 1.0;
+    return A[i + d * lda];
+  }
+};
+
+// Bottom half of a tree-node panel's reflectors: reflector c = k + p is
+// [e_c (top); u_c (bottom rows 0..c)] and u_c is stored in column c of the
+// right child's slot.  Loads bypass L1 (the slot was written by another
+// block).  The e_c halves are the identity "top" block of the application.
+struct MergeV {
+  const double* Rb;
+  int64_t M, k;
+  int nbk;
+  __device__ __forceinline__ double operator()(int64_t i, int p) const {
+    if (p >= nbk) return 0.0;
+    const int64_t c = k + p;
+    return (i <= c) ? ldcg(Rb + i + c * M) : 0.0;
+  }
+};
+
+template <bool CG>
+__device__ __forceinline__ double ld_c(const double* p) {
+  if (CG) return ldcg(p);
+  return *p;
 }
 
-// C[k:h, 0:ncols] := (I - V op(T) V^T) C[k:h, 0:ncols] with op(T) = T^T
-// (TRANS: applies Q_panel^T, the factorisation's trailing update) or T
-// (applies Q_panel, the modes product).  The two contractions W = V^T C and
-// C -= V W' run on the FP64 tensor pipe (mma.sync m8n8k4); W is reduced over
-// K slices in a fixed order, so results are bitwise repeatable.
-template <bool TRANS>
-__device__ void apply_block_reflector(const double* A, int64_t lda, int64_t k, int nbk, int64_t h,
-                                      double* C, int64_t ldc, int ncols, const double* sT,
-                                      double* sW, double* sWp) {
+// C[r0:r1, 0:ncols] := (I - V op(T) V^T) C[r0:r1, 0:ncols] with op(T) = T^T
+// (TRANS: applies Q_panel^T, the factorisations' trailing update) or T
+// (applies Q_panel, the modes product).  V(i, p) comes from the functor.  If
+// `top` is given, the panel's reflectors also carry an identity block acting
+// on the nbk rows top[0:nbk, 0:ncols] (ld ldtop): the tree-node case.
+// The contractions W = V^T C and C -= V W' run on the FP64 tensor pipe
+// (mma.sync m8n8k4); W is reduced over row slices in a fixed order, so
+// results are bitwise repeatable.  CG: load C through L2 only.
+template <bool TRANS, bool CG, class VF>
+__device__ void block_reflector(const VF& V, int nbk, int64_t r0, int64_t r1, double* C, int64_t ldc,
+                                int ncols, double* top, int64_t ldtop, const double* sT, double* sW,
+                                double* sWp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int g = lane >> 2, t = lane & 3;
-  const int64_t L = h - k;
+  const int64_t L = r1 - r0;
   const int64_t nsteps = (L + 3) / 4;
   for (int c0 = 0; c0 < ncols; c0 += kCW) {
     const int wc = min(kCW, ncols - c0);
@@ -70,14 +99,14 @@ __device__ void apply_block_reflector(const double* A, int64_t lda, int64_t k, i
 #pragma unroll
         for (int tt = 0; tt < kTPW; ++tt) acc[mt][tt][0] = acc[mt][tt][1] = 0.0;
       for (int64_t stp = sb; stp < se; ++stp) {
-        const int64_t row = k + stp * 4 + t;
-        const double a0 = vval(A, lda, k, nbk, h, row, g);
-        const double a1 = vval(A, lda, k, nbk, h, row, 8 + g);
-        const bool rok = row < h;
+        const int64_t row = r0 + stp * 4 + t;
+        const bool rok = row < r1;
+        const double a0 = rok ? V(row, g) : 0.0;
+        const double a1 = rok ? V(row, 8 + g) : 0.0;
 #pragma unroll
         for (int tt = 0; tt < kTPW; ++tt) {
           const int col = (gi * kTPW + tt) * 8 + g;
-          const double b = (rok && col < wc) ? C[row + (int64_t)(c0 + col) * ldc] : 0.0;
+          const double b = (rok && col < wc) ? ld_c<CG>(C + row + (int64_t)(c0 + col) * ldc) : 0.0;
           dmma884(acc[0][tt][0], acc[0][tt][1], a0, b);
           dmma884(acc[1][tt][0], acc[1][tt][1], a1, b);
         }
@@ -96,6 +125,10 @@ __device__ void apply_block_reflector(const double* A, int64_t lda, int64_t k, i
     for (int idx = threadIdx.x; idx < kNB * WcP; idx += blockDim.x) {
       double s = 0.0;
       for (int si = 0; si < S; ++si) s += sWp[si * kNB * WcP + idx];
+      if (top) {
+        const int p = idx / WcP, col = idx - p * WcP;
+        if (p < nbk && col < wc) s += ld_c<true>(top + p + (int64_t)(c0 + col) * ldtop);
+      }
       sW[idx] = s;
     }
     __syncthreads();
@@ -111,20 +144,27 @@ __device__ void apply_block_reflector(const double* A, int64_t lda, int64_t k, i
       sWp[idx] = -s;
     }
     __syncthreads();
+    if (top) {
+      for (int idx = threadIdx.x; idx < nbk * wc; idx += blockDim.x) {
+        const int p = idx / wc, col = idx - p * wc;
+        double* tp = top + p + (int64_t)(c0 + col) * ldtop;
+        *tp = ld_c<true>(tp) + sWp[p * WcP + col];
+      }
+    }
     // phase 3: C += V (-W')
     const int64_t nrt = (L + 7) / 8;
     for (int64_t rt = warp; rt < nrt; rt += nwarps) {
-      const int64_t i0 = k + rt * 8;
+      const int64_t i0 = r0 + rt * 8;
+      const int64_t row = i0 + g;
+      const bool rok = row < r1;
       double a[4];
 #pragma unroll
-      for (int ks = 0; ks < 4; ++ks) a[ks] = vval(A, lda, k, nbk, h, i0 + g, ks * 4 + t);
-      const int64_t row = i0 + g;
-      const bool rok = row < h;
+      for (int ks = 0; ks < 4; ++ks) a[ks] = rok ? V(row, ks * 4 + t) : 0.0;
       for (int ct = 0; ct < NT; ++ct) {
         const int col = ct * 8 + 2 * t;
         double* cp = C + row + (int64_t)(c0 + col) * ldc;
-        double d0 = (rok && col < wc) ? cp[0] : 0.0;
-        double d1 = (rok && col + 1 < wc) ? cp[ldc] : 0.0;
+        double d0 = (rok && col < wc) ? ld_c<CG>(cp) : 0.0;
+        double d1 = (rok && col + 1 < wc) ? ld_c<CG>(cp + ldc) : 0.0;
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks)
           dmma884(d0, d1, a[ks], sWp[(ks * 4 + t) * WcP + ct * 8 + g]);
@@ -208,54 +248,111 @@ __device__ void panel_factor(double* A, int64_t lda, int64_t k, int nbk, int64_t
   }
 }
 
-// QR of the stacked pair [Rt; Rb] of two upper-triangular M x M factors
-// (the buffer C of Alg. 1, receiver's R on top).  Reflector c touches only
-// row c of the top and rows 0..c of the bottom, so it is stored in column c
-// of Rb (rows 0..c) and the merged R overwrites Rt.  Loads bypass L1: the
-// partner's R was written by another block.
-__device__ void tree_merge(double* Rt, double* Rb, double* tau, int64_t M, double* su,
-                           double* sred) {
+// Panel factorisation of columns [k, k+nbk) of the stacked pair [Rt; Rb]
+// of two upper-triangular M x M factors (the buffer C of Alg. 1, receiver's
+// R on top).  Reflector c touches only row c of the top and rows 0..c of the
+// bottom: v_c = [e_c; u_c], u_c stored in column c of Rb (rows 0..c), the
+// merged R overwrites Rt.  T (row-major, upper) follows the same forward
+// recurrence as the leaves, with v_p^T v_c = u_p^T u_c (the e parts are
+// disjoint).  Loads bypass L1: the partner's slot was written by another
+// block.  sout needs 2 kNB doubles.
+__device__ void merge_panel_factor(double* Rt, double* Rb, int64_t M, int64_t k, int nbk,
+                                   double* tau_out, double* sT, double* sred, double* sout) {
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
-  for (int64_t c = 0; c < M; ++c) {
-    if (warp == 0) {
-      double xx = 0.0;
-      for (int64_t i = lane; i <= c; i += 32) {
-        const double v = ldcg(Rb + i + c * M);
-        xx += v * v;
-      }
-      xx = warp_sum(xx);
-      if (lane == 0) {
-        const double alpha = ldcg(Rt + c + c * M);
-        double tc = 0.0, beta = alpha, scale = 0.0;
-        if (xx != 0.0) {
-          const double nrm = sqrt(alpha * alpha + xx);
-          beta = (alpha >= 0.0) ? -nrm : nrm;
-          tc = (beta - alpha) / beta;
-          scale = 1.0 / (alpha - beta);
-        }
-        sred[0] = tc;
-        sred[1] = scale;
-        Rt[c + c * M] = beta;
-        tau[c] = tc;
-      }
+  double* sd = sout + kNB;   // tau_c * (v_c^T column) of the panel columns
+  double xx;
+  {
+    double v[1] = {0.0};
+    for (int64_t i = tid; i <= k; i += nthr) {
+      const double a = ldcg(Rb + i + k * M);
+      v[0] += a * a;
     }
-    __syncthreads();
-    const double tc = sred[0], scale = sred[1];
+    block_sum<1>(v, sred, sout);
+    xx = sout[0];
+  }
+  for (int jj = 0; jj < nbk; ++jj) {
+    const int64_t c = k + jj;
+    const double alpha = ldcg(Rt + c + c * M);
+    double tau_c = 0.0, beta = alpha, scale = 0.0;
+    if (xx != 0.0) {
+      const double nrm = sqrt(alpha * alpha + xx);
+      beta = (alpha >= 0.0) ? -nrm : nrm;
+      tau_c = (beta - alpha) / beta;
+      scale = 1.0 / (alpha - beta);
+    }
+    // pass A: u_c = scale * bottom column c; dots of u_c with the bottom part
+    // of the later panel columns (q > jj) and with earlier reflectors (q < jj)
+    double acc[kNB];
+#pragma unroll
+    for (int q = 0; q < kNB; ++q) acc[q] = 0.0;
     for (int64_t i = tid; i <= c; i += nthr) {
       const double u = ldcg(Rb + i + c * M) * scale;
       Rb[i + c * M] = u;
-      su[i] = u;
+#pragma unroll
+      for (int q = 0; q < kNB; ++q)
+        if (q < nbk && q != jj) acc[q] += u * ldcg(Rb + i + (k + q) * M);
+    }
+    block_sum<kNB>(acc, sred, sout);
+    if (tid == 0) {
+      Rt[c + c * M] = beta;
+      tau_out[jj] = tau_c;
+      for (int p = 0; p < jj; ++p) {
+        double s = 0.0;
+        for (int q = p; q < jj; ++q) s += sT[p * kNB + q] * sout[q];
+        sT[p * kNB + jj] = -tau_c * s;
+      }
+      sT[jj * kNB + jj] = tau_c;
+    }
+    if (tid > jj && tid < nbk) {
+      // the e_c part of v_c contributes the top entry Rt[c, k+q]
+      double* tp = Rt + c + (k + tid) * M;
+      const double d = (sout[tid] + ldcg(tp)) * tau_c;
+      sd[tid] = d;
+      *tp = ldcg(tp) - d;
     }
     __syncthreads();
-    if (tc != 0.0) {
-      for (int64_t cc = c + 1 + warp; cc < M; cc += nwarps) {
-        double s = 0.0;
-        for (int64_t i = lane; i <= c; i += 32) s += su[i] * ldcg(Rb + i + cc * M);
-        s = (warp_sum(s) + ldcg(Rt + c + cc * M)) * tc;
-        for (int64_t i = lane; i <= c; i += 32) Rb[i + cc * M] = ldcg(Rb + i + cc * M) - s * su[i];
-        if (lane == 0) Rt[c + cc * M] = ldcg(Rt + c + cc * M) - s;
+    // pass B: bottom rows 0..c of the later panel columns; squared norm of
+    // the next column's bottom rows 0..c+1
+    double nx[1] = {0.0};
+    if (jj + 1 < nbk) {
+      for (int64_t i = tid; i <= c + 1; i += nthr) {
+        const double u = (i <= c) ? ldcg(Rb + i + c * M) : 0.0;
+#pragma unroll
+        for (int q = 0; q < kNB; ++q) {
+          if (q > jj && q < nbk) {
+            double* bp = Rb + i + (k + q) * M;
+            double a = ldcg(bp);
+            if (i <= c) {
+              a -= sd[q] * u;
+              *bp = a;
+            }
+            if (q == jj + 1) nx[0] += a * a;
+          }
+        }
       }
+    }
+    block_sum<1>(nx, sred, sout);
+    xx = sout[0];
+  }
+}
+
+// QR of [Rt; Rb] by panels of kNB columns: structured panel factorisation,
+// then the block reflector applied to the trailing columns on the FP64
+// tensor pipe (bottom rows 0..k+nbk-1 through u, top rows k..k+nbk-1 as the
+// identity block).  Flops (2/3) M^3 as in the paper's cost model.
+__device__ void tree_merge(double* Rt, double* Rb, double* tau, int64_t M, double* sT, double* sred,
+                           double* sout, double* sW, double* sWp) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int64_t k = 0; k < M; k += kNB) {
+    const int nbk = (int)((M - k) < kNB ? (M - k) : kNB);
+    for (int idx = tid; idx < kSmT; idx += nthr) sT[idx] = 0.0;
+    __syncthreads();
+    merge_panel_factor(Rt, Rb, M, k, nbk, tau + k, sT, sred, sout);
+    __syncthreads();
+    if (k + nbk < M) {
+      MergeV V{Rb, M, k, nbk};
+      block_reflector<true, true>(V, nbk, 0, k + nbk, Rb + (k + nbk) * M, M, (int)(M - k - nbk),
+                                  Rt + k + (k + nbk) * M, M, sT, sW, sWp);
     }
     __syncthreads();
   }
@@ -329,9 +426,11 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_qr_kernel(LeafArgs a) {
     __syncthreads();
     double* Tg = s.T + (leaf * s.npan + k / kNB) * kSmT;
     for (int idx = tid; idx < kSmT; idx += nthr) Tg[idx] = sT[idx];
-    if (k + nbk < M)
-      apply_block_reflector<true>(A, lda, k, nbk, h, A + (k + nbk) * lda, lda, (int)(M - k - nbk),
-                                  sT, sW, sWp);
+    if (k + nbk < M) {
+      LeafV V{A, lda, k, h, nbk};
+      block_reflector<true, false>(V, nbk, k, h, A + (k + nbk) * lda, lda, (int)(M - k - nbk),
+                                   nullptr, 0, sT, sW, sWp);
+    }
     __syncthreads();
   }
 
@@ -362,7 +461,8 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_qr_kernel(LeafArgs a) {
     __syncthreads();
     if (s_prev == 0) return;  // first to arrive: the partner merges
     __threadfence();
-    tree_merge(s.Rs + left * M * M, s.Rs + right * M * M, s.tau_tree + right * M, M, sW, sred);
+    tree_merge(s.Rs + left * M * M, s.Rs + right * M * M, s.tau_tree + right * M, M, sT, sred,
+               sout, sW, sWp);
     __threadfence();
     __syncthreads();
     node = left;
@@ -439,7 +539,8 @@ __global__ void __launch_bounds__(kLeafThreads) modes_kernel(TsqrState s, int64_
     const double* Tg = s.T + (leaf * s.npan + pan) * kSmT;
     for (int idx = tid; idx < kSmT; idx += nthr) sT[idx] = Tg[idx];
     __syncthreads();
-    apply_block_reflector<false>(A, s.N, k, nbk, h, C, ldu, (int)r, sT, sW, sWp);
+    LeafV V{A, s.N, k, h, nbk};
+    block_reflector<false, false>(V, nbk, k, h, C, ldu, (int)r, nullptr, 0, sT, sW, sWp);
     __syncthreads();
   }
   if (physical && w) {
