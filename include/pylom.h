@@ -122,6 +122,33 @@ pylom_status pylom_pod(const void* X, int64_t N, int64_t M, int64_t ldx, int xty
                        void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
+ * pylom_pod_backward -- hand-written adjoint of pylom_pod (no counterpart in
+ * the paper; it differentiates the composition of Alg. 2, Alg. 1 and Eqs.
+ * svdqr1-svdqr3).  Given cotangents dU (of the r returned modes), dS and
+ * dVT, writes dX, the cotangent of X.  Q is recomputed from the leaf and
+ * tree reflectors that the forward call left in its workspace (Q^T dU by
+ * the leaf reflectors and a bottom-up tree pass; Q [B; 0] by the top-down
+ * pass); the square SVD adjoint of R runs in binary64 on M x M matrices.
+ *  fwd_ws, fwd_ws_bytes  the workspace of the pylom_pod call being
+ *                        differentiated, unchanged since (same N, M,
+ *                        leaf_rows, r_max, w, remove_mean, mode_kind).
+ *  r       number of modes whose cotangent dU holds (0 <= r <= r_max).
+ *  S, VT   that call's singular values and right vectors (ldvt >= M).
+ *  dU      N x r (lddu >= N) or NULL; dS: M or NULL; dVT: M x M or NULL.
+ *  dX      out, N x M (lddx >= N), element type dxtype (F32 or F64).
+ * Degenerate singular values (s_i == s_j) contribute no coupling term; the
+ * singular values of the r modes that carry a cotangent must be nonzero
+ * (R itself may be singular, as it is once the mean is removed).
+ * ------------------------------------------------------------------------ */
+size_t pylom_pod_backward_workspace_size(int64_t N, int64_t M, int64_t leaf_rows, int64_t r);
+pylom_status pylom_pod_backward(const void* fwd_ws, size_t fwd_ws_bytes, int64_t N, int64_t M,
+                                int64_t leaf_rows, int64_t r_max, int64_t r, const double* w,
+                                int remove_mean, int mode_kind, const double* S, const double* VT,
+                                int64_t ldvt, const double* dU, int64_t lddu, const double* dS,
+                                const double* dVT, int64_t lddvt, void* dX, int64_t lddx, int dxtype,
+                                void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
  * pylom_tsqr -- tall-skinny QR of Alg. 1: A = Q [R; 0] (Eq. svdqr1).
  *  A      in   N x M, lda >= N, xtype F32 or F64 (not modified).
  *  R      out  M x M upper triangular (zeros below the diagonal), ldr >= M.

@@ -61,6 +61,8 @@ def _load():
         lib.oracle_pod.restype = ctypes.c_int
         lib.oracle_tsqr.argtypes = [_dp, _i64, _i64, _i64, _dp, _i64, _dp, _i64]
         lib.oracle_matmul.argtypes = [ctypes.c_int, _dp, _dp, _dp, _i64, _i64, _i64, _i64, _i64, _i64]
+        lib.oracle_pod_loss_grad.argtypes = [_dp, _i64, _i64, _i64, _dp, ctypes.c_int, _i64, _dp, _i64]
+        lib.oracle_pod_loss_grad.restype = ctypes.c_double
         _lib = lib
     return _lib
 
@@ -177,3 +179,14 @@ def matmul(A, B, transA=False):
     C = np.zeros((m, n), order="F")
     _load().oracle_matmul(int(bool(transA)), _p(A), _p(B), _p(C), m, n, k, A.shape[0], B.shape[0], m)
     return C
+
+
+def pod_loss_grad(X, r, w=None, remove_mean=False, want_grad=True):
+    """Truncated-POD reconstruction loss L = sum_{i>r} s_i^2 of Y_w and its
+    closed-form gradient dL/dX (valid where s_r > s_{r+1})."""
+    X = _f64(X)
+    N, M = X.shape
+    wv = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+    G = np.zeros((N, M), order="F") if want_grad else None
+    L = _load().oracle_pod_loss_grad(_p(X), N, M, N, _p(wv), int(bool(remove_mean)), int(r), _p(G), N)
+    return float(L), G

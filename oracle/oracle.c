@@ -360,3 +360,56 @@ void oracle_matmul(int transA, const double* A, const double* B, double* C,
       C[j * ldc + i] = s;
     }
 }
+
+/* ------------------------------------------------------------------------
+ * Truncated-POD reconstruction loss and its gradient.
+ * L(X) = || (I - U_r U_r^T) Y_w ||_F^2 = sum_{i>r} s_i^2, with Y_w the
+ * weighted (and optionally centred) snapshot matrix of Alg. 2 and U_r its
+ * r leading left singular vectors (Eqs. svdqr1-svdqr3).  Where s_r > s_{r+1}
+ * the derivative of sum_{i<=r} s_i^2 is 2 U_r U_r^T Y_w, so
+ *   dL/dY_w = 2 (I - U_r U_r^T) Y_w,
+ *   dL/dX   = diag(sqrt w) dL/dY_w (I - 1 1^T / M if the mean is removed).
+ * Returns L; writes G (N x M, ldg) when G != NULL.
+ * ------------------------------------------------------------------------ */
+double oracle_pod_loss_grad(const double* X, int64_t N, int64_t M, int64_t ldx,
+                            const double* w, int remove_mean, int64_t r, double* G,
+                            int64_t ldg) {
+  double* Y = (double*)malloc(sizeof(double) * N * M);
+  double* U = (double*)malloc(sizeof(double) * N * (r > 0 ? r : 1));
+  double* S = (double*)malloc(sizeof(double) * M);
+  double* VT = (double*)malloc(sizeof(double) * M * M);
+  double* C = (double*)malloc(sizeof(double) * (r > 0 ? r : 1) * M);
+  int64_t rr = 0;
+  oracle_center_weight(X, N, M, ldx, w, remove_mean, Y, N, NULL);
+  oracle_pod(X, N, M, ldx, w, remove_mean, 0.0, r, 0, U, N, S, VT, M, NULL, &rr, 60);
+  double L = 0.0;
+  for (int64_t i = r; i < M; ++i) L += S[i] * S[i];
+  if (G) {
+    /* C = U_r^T Y_w (r x M), then G = 2 (Y_w - U_r C) */
+#pragma omp parallel for schedule(static)
+    for (int64_t m = 0; m < M; ++m)
+      for (int64_t i = 0; i < r; ++i) {
+        double s = 0.0;
+        for (int64_t n = 0; n < N; ++n) s += U[i * N + n] * Y[m * N + n];
+        C[m * r + i] = s;
+      }
+#pragma omp parallel for schedule(static)
+    for (int64_t n = 0; n < N; ++n) {
+      double swn = w ? sqrt(w[n]) : 1.0;
+      double rowsum = 0.0;
+      for (int64_t m = 0; m < M; ++m) {
+        double p = 0.0;
+        for (int64_t i = 0; i < r; ++i) p += U[i * N + n] * C[m * r + i];
+        double g = 2.0 * (Y[m * N + n] - p) * swn;
+        G[m * ldg + n] = g;
+        rowsum += g;
+      }
+      if (remove_mean) {
+        double mu = rowsum / (double)M;
+        for (int64_t m = 0; m < M; ++m) G[m * ldg + n] -= mu;
+      }
+    }
+  }
+  free(Y); free(U); free(S); free(VT); free(C);
+  return L;
+}

@@ -36,6 +36,7 @@ EXPORTS = (
     "pylom_svd_small_workspace_size", "pylom_svd_small", "pylom_matmul_workspace_size",
     "pylom_matmul", "pylom_profile_begin", "pylom_profile_end",
     "pylom_probe_scratch_bytes", "pylom_probe_fp64_peak", "pylom_svd_small_noalloc",
+    "pylom_pod_backward_workspace_size", "pylom_pod_backward",
 )
 PROFILE_PHASES = ("leaf_qr_tree", "svd_small", "down_pass", "modes")
 
@@ -90,6 +91,11 @@ def load_library(path: str = LIB_PATH):
     lib.pylom_profile_begin.argtypes = [_int]
     lib.pylom_profile_end.restype = _int
     lib.pylom_profile_end.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_int)]
+    lib.pylom_pod_backward_workspace_size.restype = _sz
+    lib.pylom_pod_backward_workspace_size.argtypes = [_i64, _i64, _i64, _i64]
+    lib.pylom_pod_backward.restype = _int
+    lib.pylom_pod_backward.argtypes = [_vp, _sz, _i64, _i64, _i64, _i64, _i64, _vp, _int, _int, _vp, _vp,
+                                       _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, _int, _vp, _sz, _vp]
     lib.pylom_svd_small_noalloc.restype = _int
     lib.pylom_svd_small_noalloc.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _int, _vp, _vp]
     lib.pylom_probe_scratch_bytes.restype = _sz
@@ -330,3 +336,76 @@ def matmul(A, B, transA=False, stream=None):
                           _ld(B), _ld(C), _dptr(ws), ws.numel(), _stream(stream))
     _raise(st, "pylom_matmul")
     return C
+
+
+def pod_backward(fwd: PodResult, X_shape, w, remove_mean, mode_kind, leaf_rows, r_max, dU=None, dS=None,
+                 dVT=None, dx_dtype=None, stream=None, check=True):
+    """Cotangent of X for the pylom_pod call that produced `fwd` (its
+    workspace must be unchanged).  dU: N x r (r = fwd.r), dS: M, dVT: M x M."""
+    torch = _torch()
+    lib = load_library()
+    N, M = X_shape
+    dev = fwd.S.device
+    dx_dtype = dx_dtype or torch.float64
+    dxt = {torch.float32: F32, torch.float64: F64}[dx_dtype]
+    r = fwd.r
+    if dU is not None:
+        dU = _colmajor(dU.to(torch.float64))
+    if dS is not None:
+        dS = dS.to(torch.float64).contiguous()
+    if dVT is not None:
+        dVT = _colmajor(dVT.to(torch.float64))
+    if w is not None:
+        w = w.to(device=dev, dtype=torch.float64).contiguous()
+    need = lib.pylom_pod_backward_workspace_size(N, M, leaf_rows, r)
+    if need == 0:
+        _raise(ERR_SHAPE, "pylom_pod_backward_workspace_size")
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    dX = empty_colmajor(N, M, dx_dtype, dev)
+    st = lib.pylom_pod_backward(_dptr(fwd.workspace), fwd.workspace.numel(), N, M, leaf_rows, r_max, r,
+                                _dptr(w), int(bool(remove_mean)), int(mode_kind), _dptr(fwd.S), _dptr(fwd.VT),
+                                _ld(fwd.VT), _dptr(dU), _ld(dU) if dU is not None else N, _dptr(dS),
+                                _dptr(dVT), _ld(dVT) if dVT is not None else M, _dptr(dX), _ld(dX), dxt,
+                                _dptr(ws), ws.numel(), _stream(stream))
+    _raise(st, "pylom_pod_backward")
+    if check:
+        st, _, _ = workspace_status(ws, stream)
+        _raise(st, "pylom_pod_backward (device)")
+    return dX
+
+
+def _make_pod_function():
+    import torch
+
+    class PodFn(torch.autograd.Function):
+        """POD as a differentiable operation: forward = pylom_pod (modes,
+        singular values, right vectors), backward = pylom_pod_backward, the
+        hand-written TSQR + small-SVD adjoint.  Returns (U_r, S, VT)."""
+
+        @staticmethod
+        def forward(ctx, X, w, r, remove_mean, mode_kind, leaf_rows):
+            res = pod(X.detach(), w=w, remove_mean=remove_mean, energy=0.0, r_max=r, mode_kind=mode_kind,
+                      leaf_rows=leaf_rows, check=True)
+            ctx.fwd = res
+            ctx.meta = (tuple(X.shape), X.dtype, w, remove_mean, mode_kind, leaf_rows, r)
+            return res.U.clone(), res.S.clone(), res.VT.clone()
+
+        @staticmethod
+        def backward(ctx, gU, gS, gVT):
+            shape, dtype, w, remove_mean, mode_kind, leaf_rows, r = ctx.meta
+            dX = pod_backward(ctx.fwd, shape, w, remove_mean, mode_kind, leaf_rows, r, dU=gU, dS=gS, dVT=gVT,
+                              dx_dtype=dtype)
+            return dX, None, None, None, None, None
+
+    return PodFn
+
+
+_PodFn = None
+
+
+def pod_autograd(X, r, w=None, remove_mean=False, mode_kind=MODES_ORTHONORMAL, leaf_rows=0):
+    """Differentiable POD: (U_r, S, VT) with the hand-written adjoint."""
+    global _PodFn
+    if _PodFn is None:
+        _PodFn = _make_pod_function()
+    return _PodFn.apply(X, w, int(r), bool(remove_mean), int(mode_kind), int(leaf_rows))

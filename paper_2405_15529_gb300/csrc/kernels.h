@@ -59,6 +59,15 @@ cudaError_t launch_modes_fp64(const TsqrState& s, const double* Ur, int64_t ldur
                               const double* w, int physical, double* U, int64_t ldu,
                               int64_t* r_out, cudaStream_t st, cudaEvent_t mid = nullptr);
 
+// Adjoint of the POD path (pod_backward.cu).  fs: the forward's TSQR state
+// (reflectors, T, tree); UR/S/VT: the forward's small-SVD factors.
+size_t pod_backward_bytes(int64_t N, int64_t M, int64_t P, int64_t r);
+cudaError_t launch_pod_backward(const TsqrState& fs, const double* UR, const double* S, const double* VT,
+                                int64_t ldvt, const double* dU, int64_t lddu, const double* dS,
+                                const double* dVT, int64_t lddvt, const double* w, int remove_mean,
+                                int physical, int64_t r, void* dX, int64_t lddx, int dxtype,
+                                char* bw_base, cudaStream_t st);
+
 // Records a message for pylom_last_error() on the calling host thread.
 void set_error_message(const char* fmt, ...);
 

@@ -1,0 +1,167 @@
+// reflectors.cuh -- shared device code of the FP64 TSQR kernels: the
+// shared-memory plan of a leaf-sized block, the reflector accessors of leaf
+// panels and tree-node panels, and the block-reflector application on the
+// FP64 tensor pipe.  Included by tsqr_fp64.cu and pod_backward.cu.
+#pragma once
+#include "kernels.h"
+
+namespace pylom {
+
+constexpr int kLeafThreads = 256;
+constexpr int kCW = 256;   // column chunk of a block-reflector application
+constexpr int kTPW = 4;    // 8-column tiles per warp in W = V^T C
+
+// Shared-memory plan of the leaf / modes kernels (doubles).
+constexpr int kSmT = kNB * kNB;
+constexpr int kSmRed = kNB * 32;
+constexpr int kSmOut = 32;
+constexpr int kSmW = kNB * kCW;
+constexpr size_t kLeafSmemBytes = sizeof(double) * (kSmT + kSmRed + kSmOut + 2 * kSmW);
+
+// Entry (i, p) of a leaf panel's reflector matrix V (panel starts at
+// column k, nbk reflectors, h rows): zero above the diagonal, one on it,
+// stored below.
+struct LeafV {
+  const double* A;
+  int64_t lda, k, h;
+  int nbk;
+  __device__ __forceinline__ double operator()(int64_t i, int p) const {
+    if (p >= nbk || i >= h) return 0.0;
+    const int64_t d = k + p;
+    if (i < d) return 0.0;
+    if (i == d) return 1.0;
+    return A[i + d * lda];
+  }
+};
+
+// Bottom half of a tree-node panel's reflectors: reflector c = k + p is
+// [e_c (top); u_c (bottom rows 0..c)] and u_c is stored in column c of the
+// right child's slot.  Loads bypass L1 (the slot was written by another
+// block).  The e_c halves are the identity "top" block of the application.
+struct MergeV {
+  const double* Rb;
+  int64_t M, k;
+  int nbk;
+  __device__ __forceinline__ double operator()(int64_t i, int p) const {
+    if (p >= nbk) return 0.0;
+    const int64_t c = k + p;
+    return (i <= c) ? ldcg(Rb + i + c * M) : 0.0;
+  }
+};
+
+template <bool CG>
+__device__ __forceinline__ double ld_c(const double* p) {
+  if (CG) return ldcg(p);
+  return *p;
+}
+
+// C[r0:r1, 0:ncols] := (I - V op(T) V^T) C[r0:r1, 0:ncols] with op(T) = T^T
+// (TRANS: applies Q_panel^T, the factorisations' trailing update) or T
+// (applies Q_panel, the modes product).  V(i, p) comes from the functor.  If
+// `top` is given, the panel's reflectors also carry an identity block acting
+// on the nbk rows top[0:nbk, 0:ncols] (ld ldtop): the tree-node case.
+// The contractions W = V^T C and C -= V W' run on the FP64 tensor pipe
+// (mma.sync m8n8k4); W is reduced over row slices in a fixed order, so
+// results are bitwise repeatable.  CG: load C through L2 only.
+template <bool TRANS, bool CG, class VF>
+__device__ void block_reflector(const VF& V, int nbk, int64_t r0, int64_t r1, double* C, int64_t ldc,
+                                int ncols, double* top, int64_t ldtop, const double* sT, double* sW,
+                                double* sWp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int64_t L = r1 - r0;
+  const int64_t nsteps = (L + 3) / 4;
+  for (int c0 = 0; c0 < ncols; c0 += kCW) {
+    const int wc = min(kCW, ncols - c0);
+    const int NT = (wc + 7) / 8;
+    const int G = (NT + kTPW - 1) / kTPW;
+    const int S = (G >= nwarps) ? 1 : nwarps / G;
+    const int WcP = G * kTPW * 8;
+    // phase 1: partial W = V^T C over S slices of the rows
+    for (int u = warp; u < G * S; u += nwarps) {
+      const int gi = u % G, si = u / G;
+      const int64_t sb = (nsteps * si) / S, se = (nsteps * (si + 1)) / S;
+      double acc[2][kTPW][2];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int tt = 0; tt < kTPW; ++tt) acc[mt][tt][0] = acc[mt][tt][1] = 0.0;
+      for (int64_t stp = sb; stp < se; ++stp) {
+        const int64_t row = r0 + stp * 4 + t;
+        const bool rok = row < r1;
+        const double a0 = rok ? V(row, g) : 0.0;
+        const double a1 = rok ? V(row, 8 + g) : 0.0;
+#pragma unroll
+        for (int tt = 0; tt < kTPW; ++tt) {
+          const int col = (gi * kTPW + tt) * 8 + g;
+          const double b = (rok && col < wc) ? ld_c<CG>(C + row + (int64_t)(c0 + col) * ldc) : 0.0;
+          dmma884(acc[0][tt][0], acc[0][tt][1], a0, b);
+          dmma884(acc[1][tt][0], acc[1][tt][1], a1, b);
+        }
+      }
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int tt = 0; tt < kTPW; ++tt) {
+          const int p = mt * 8 + g;
+          const int col = (gi * kTPW + tt) * 8 + 2 * t;
+          sWp[(si * kNB + p) * WcP + col] = acc[mt][tt][0];
+          sWp[(si * kNB + p) * WcP + col + 1] = acc[mt][tt][1];
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kNB * WcP; idx += blockDim.x) {
+      double s = 0.0;
+      for (int si = 0; si < S; ++si) s += sWp[si * kNB * WcP + idx];
+      if (top) {
+        const int p = idx / WcP, col = idx - p * WcP;
+        if (p < nbk && col < wc) s += ld_c<true>(top + p + (int64_t)(c0 + col) * ldtop);
+      }
+      sW[idx] = s;
+    }
+    __syncthreads();
+    // phase 2: sWp = -op(T) W
+    for (int idx = threadIdx.x; idx < kNB * WcP; idx += blockDim.x) {
+      const int p = idx / WcP, col = idx - p * WcP;
+      double s = 0.0;
+      if (TRANS) {
+        for (int q = 0; q <= p; ++q) s += sT[q * kNB + p] * sW[q * WcP + col];
+      } else {
+        for (int q = p; q < kNB; ++q) s += sT[p * kNB + q] * sW[q * WcP + col];
+      }
+      sWp[idx] = -s;
+    }
+    __syncthreads();
+    if (top) {
+      for (int idx = threadIdx.x; idx < nbk * wc; idx += blockDim.x) {
+        const int p = idx / wc, col = idx - p * wc;
+        double* tp = top + p + (int64_t)(c0 + col) * ldtop;
+        *tp = ld_c<true>(tp) + sWp[p * WcP + col];
+      }
+    }
+    // phase 3: C += V (-W')
+    const int64_t nrt = (L + 7) / 8;
+    for (int64_t rt = warp; rt < nrt; rt += nwarps) {
+      const int64_t i0 = r0 + rt * 8;
+      const int64_t row = i0 + g;
+      const bool rok = row < r1;
+      double a[4];
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) a[ks] = rok ? V(row, ks * 4 + t) : 0.0;
+      for (int ct = 0; ct < NT; ++ct) {
+        const int col = ct * 8 + 2 * t;
+        double* cp = C + row + (int64_t)(c0 + col) * ldc;
+        double d0 = (rok && col < wc) ? ld_c<CG>(cp) : 0.0;
+        double d1 = (rok && col + 1 < wc) ? ld_c<CG>(cp + ldc) : 0.0;
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks)
+          dmma884(d0, d1, a[ks], sWp[(ks * 4 + t) * WcP + ct * 8 + g]);
+        if (rok && col < wc) cp[0] = d0;
+        if (rok && col + 1 < wc) cp[ldc] = d1;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace pylom

@@ -1,0 +1,136 @@
+"""GPU parity of the hand-written POD adjoint (pylom_pod_backward behind a
+torch.autograd.Function) against the oracle's closed-form gradient of the
+truncated-POD reconstruction loss, against central finite differences of
+the oracle's forward, and against torch.linalg.svd autograd."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+pg = pytest.importorskip("paper_2405_15529_gb300")
+
+
+def _dev(X):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(X).T)).to("cuda").t()
+
+
+def _loss_torch(X, w, U):
+    """L = || Y_w - U U^T Y_w ||_F^2 with Y_w = sqrt(w) X (no mean)."""
+    Yw = X.double() * torch.sqrt(w)[:, None] if w is not None else X.double()
+    return torch.sum((Yw - U @ (U.T @ Yw)) ** 2)
+
+
+def test_adjoint_matches_closed_form_and_finite_differences():
+    # N = 512, M = 16, r = 4, binary64; separated spectrum s_i = 10^(-6 i / 15)
+    N, M, r = 512, 16, 4
+    X, w, s = synth.known_spectrum(N, M, weights=True, seeds=(7, 8, 9))
+    Xd = _dev(X).requires_grad_(True)
+    wd = torch.from_numpy(w).cuda()
+    U, S, VT = pg.pod_autograd(Xd, r, w=wd, remove_mean=False, leaf_rows=64)
+    L = _loss_torch(Xd, wd, U)
+    L.backward()
+    G = Xd.grad.cpu().numpy()
+    L_ref, G_ref = oracle.pod_loss_grad(X, r, w=w, remove_mean=False)
+    assert L.item() == pytest.approx(L_ref, rel=1e-9, abs=1e-12 * np.sum(s ** 2))
+    rel = np.linalg.norm(G - G_ref) / np.linalg.norm(G_ref)
+    assert rel <= 1e-6, rel
+    h = 1e-6 * np.abs(X).max()
+    rng = np.random.default_rng(10)
+    for _ in range(12):
+        n, m = int(rng.integers(N)), int(rng.integers(M))
+        Xp = X.copy(); Xp[n, m] += h
+        Xm = X.copy(); Xm[n, m] -= h
+        fd = (oracle.pod_loss_grad(Xp, r, w=w, want_grad=False)[0]
+              - oracle.pod_loss_grad(Xm, r, w=w, want_grad=False)[0]) / (2 * h)
+        assert G[n, m] == pytest.approx(fd, rel=1e-6, abs=1e-6 * np.abs(G_ref).max())
+
+
+def _signed_svd_reference(Yw, r):
+    """torch.linalg.svd with the library's sign rule applied (the largest
+    |entry| of each right vector positive, lowest index on ties)."""
+    U, S, Vh = torch.linalg.svd(Yw, full_matrices=False)
+    with torch.no_grad():
+        k = torch.argmax(torch.abs(Vh), dim=1)
+        sg = torch.sign(Vh[torch.arange(Vh.shape[0]), k])
+    return U[:, :r] * sg[None, :r], S, Vh * sg[:, None]
+
+
+@pytest.mark.parametrize("remove_mean,mode_kind", [(True, pg.MODES_ORTHONORMAL),
+                                                   (False, pg.MODES_PHYSICAL)])
+def test_adjoint_general_cotangents_match_torch_svd(remove_mean, mode_kind):
+    N, M, r = 300, 12, 5
+    rng = np.random.default_rng(11)
+    X = np.asfortranarray(rng.standard_normal((N, M)) * np.logspace(0, -2, M)[None, :] + 1.0)
+    w = synth.log_uniform_weights(N, seed=12)
+    gU = rng.standard_normal((N, r)); gS = rng.standard_normal(M); gVT = rng.standard_normal((M, M))
+    if remove_mean:
+        # mean removal makes Y_w rank M-1: the last singular pair is an
+        # arbitrary null direction, and a loss may not depend on it
+        gS[-1] = 0.0
+        gVT[-1, :] = 0.0
+    # ours
+    Xd = _dev(X).requires_grad_(True)
+    wd = torch.from_numpy(w).cuda()
+    U, S, VT = pg.pod_autograd(Xd, r, w=wd, remove_mean=remove_mean, mode_kind=mode_kind, leaf_rows=40)
+    L = (torch.sum(U * torch.from_numpy(gU).cuda()) + torch.sum(S * torch.from_numpy(gS).cuda())
+         + torch.sum(VT * torch.from_numpy(gVT).cuda()))
+    L.backward()
+    G = Xd.grad.cpu().numpy()
+    # reference: torch.linalg.svd autograd on the CPU in binary64
+    Xc = torch.from_numpy(np.array(X)).requires_grad_(True)
+    wc = torch.from_numpy(w)
+    Y = Xc - Xc.mean(dim=1, keepdim=True) if remove_mean else Xc
+    Yw = Y * torch.sqrt(wc)[:, None]
+    Ur, Sr, Vhr = _signed_svd_reference(Yw, r)
+    if mode_kind == pg.MODES_PHYSICAL:
+        Ur = Ur / torch.sqrt(wc)[:, None]
+    Lr = (torch.sum(Ur * torch.from_numpy(gU)) + torch.sum(Sr * torch.from_numpy(gS))
+          + torch.sum(Vhr * torch.from_numpy(gVT)))
+    Lr.backward()
+    G_ref = Xc.grad.numpy()
+    assert np.allclose(U.detach().cpu().numpy(), Ur.detach().numpy(), atol=1e-10)
+    rel = np.linalg.norm(G - G_ref) / np.linalg.norm(G_ref)
+    assert rel <= 1e-8, rel
+
+
+def test_adjoint_full_size_fp32():
+    # 4,194,304 x 256 float32 snapshots (six-decade spectrum, weights), r = 20
+    N, M, r = 1 << 22, 256, 20
+    XT, w, s = synth.known_spectrum_torch(N, M, device="cuda", dtype=torch.float32)
+    X = XT.t().detach().requires_grad_(True)
+    U, S, VT = pg.pod_autograd(X, r, w=w, remove_mean=False)
+    L = _loss_torch(X, w, U)
+    L.backward()
+    G = X.grad
+    assert G.dtype == torch.float32
+    with torch.no_grad():
+        Yw = X.double() * torch.sqrt(w)[:, None]
+        Gc = 2.0 * torch.sqrt(w)[:, None] * (Yw - U @ (U.T @ Yw))
+        rel = (torch.linalg.norm(G.double() - Gc) / torch.linalg.norm(Gc)).item()
+        # the loss is the spectrum's tail energy
+        tail = float(np.sum(S.cpu().numpy()[r:] ** 2))
+    assert rel <= 1e-4, rel
+    assert L.item() == pytest.approx(tail, rel=1e-6)
+
+
+def test_adjoint_full_size_matches_torch_svd_autograd():
+    # the same 4,194,304 x 256 loss differentiated by torch.linalg.svd autograd
+    # on the weighted matrix in binary64 (library reference)
+    N, M, r = 1 << 22, 256, 20
+    XT, w, s = synth.known_spectrum_torch(N, M, device="cuda", dtype=torch.float32)
+    X = XT.t().detach().requires_grad_(True)
+    U, S, VT = pg.pod_autograd(X, r, w=w, remove_mean=False)
+    _loss_torch(X, w, U).backward()
+    G = X.grad.double()
+    Xr = XT.t().double().detach().requires_grad_(True)
+    Yw = Xr * torch.sqrt(w)[:, None]
+    Ur, Sr, Vhr = torch.linalg.svd(Yw, full_matrices=False)
+    Lr = torch.sum((Yw - Ur[:, :r] @ (Ur[:, :r].T @ Yw)) ** 2)
+    Lr.backward()
+    with torch.no_grad():
+        rel = (torch.linalg.norm(G - Xr.grad) / torch.linalg.norm(Xr.grad)).item()
+    assert rel <= 1e-4, rel

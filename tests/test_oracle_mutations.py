@@ -23,6 +23,8 @@ MUTATIONS = {
                      "for (int64_t j = 0; j < m; ++j) {\n    if (tau[j] == 0.0) continue;"),
     "truncation_strict": ("if (acc / total >= energy)", "if (acc / total > energy)"),
     "transposed_vt": ("VT[k * ldvt + i] = V[i * M + k];", "VT[k * ldvt + i] = V[k * M + i];"),
+    "grad_factor": ("double g = 2.0 * (Y[m * N + n] - p) * swn;", "double g = 1.0 * (Y[m * N + n] - p) * swn;"),
+    "grad_weight_missing": ("double g = 2.0 * (Y[m * N + n] - p) * swn;", "double g = 2.0 * (Y[m * N + n] - p);"),
 }
 
 

@@ -284,3 +284,35 @@ def test_matmul_local_product():
     assert np.allclose(oracle.matmul(A, B, transA=True), A.T @ B, rtol=1e-14, atol=1e-13)
     C = _rng(16).standard_normal((7, 30))
     assert np.allclose(oracle.matmul(C, B), C @ B, rtol=1e-14, atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# truncated-POD reconstruction loss and its gradient
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("remove_mean,weighted", [(False, True), (True, False), (True, True)])
+def test_loss_gradient_matches_central_differences(remove_mean, weighted):
+    N, M, r = 40, 6, 2
+    s = np.array([4.0, 2.5, 1.0, 0.5, 0.2, 0.1])
+    X, w, _ = synth.known_spectrum(N, M, s=s, weights=weighted, seeds=(61, 62, 63))
+    X = X + 0.01 * _rng(64).standard_normal((N, M))
+    L, G = oracle.pod_loss_grad(X, r, w=w, remove_mean=remove_mean)
+    # the loss is the tail energy of the spectrum
+    S = oracle.pod(X, w=w, remove_mean=remove_mean)["S"]
+    assert L == pytest.approx(np.sum(S[r:] ** 2), rel=1e-12)
+    h = 1e-6
+    for (n, m) in [(0, 0), (3, 5), (17, 2), (39, 4), (25, 1)]:
+        Xp = X.copy(); Xp[n, m] += h
+        Xm = X.copy(); Xm[n, m] -= h
+        fd = (oracle.pod_loss_grad(Xp, r, w=w, remove_mean=remove_mean, want_grad=False)[0]
+              - oracle.pod_loss_grad(Xm, r, w=w, remove_mean=remove_mean, want_grad=False)[0]) / (2 * h)
+        assert fd == pytest.approx(G[n, m], rel=1e-6, abs=1e-8 * np.abs(G).max())
+
+
+def test_loss_gradient_vanishes_for_rank_r():
+    # a rank-r snapshot matrix reconstructs exactly: L = 0 and dL/dX = 0
+    N, M, r = 50, 5, 2
+    X = _rng(70).standard_normal((N, r)) @ _rng(71).standard_normal((r, M))
+    L, G = oracle.pod_loss_grad(X, r)
+    assert abs(L) < 1e-24 * np.linalg.norm(X) ** 2 + 1e-26
+    assert np.abs(G).max() < 1e-12 * np.abs(X).max()
