@@ -63,6 +63,10 @@ def _load():
         lib.oracle_matmul.argtypes = [ctypes.c_int, _dp, _dp, _dp, _i64, _i64, _i64, _i64, _i64, _i64]
         lib.oracle_pod_loss_grad.argtypes = [_dp, _i64, _i64, _i64, _dp, ctypes.c_int, _i64, _dp, _i64]
         lib.oracle_pod_loss_grad.restype = ctypes.c_double
+        lib.oracle_zsvd.argtypes = [ctypes.c_void_p, _i64, _i64, _i64, _i64, ctypes.c_void_p, _i64, _dp,
+                                    ctypes.c_void_p, _i64, ctypes.c_int]
+        lib.oracle_zsvd.restype = ctypes.c_int
+        lib.oracle_zhouseholder_qr.argtypes = [ctypes.c_void_p, _i64, _i64, _i64, ctypes.c_void_p]
         _lib = lib
     return _lib
 
@@ -190,3 +194,27 @@ def pod_loss_grad(X, r, w=None, remove_mean=False, want_grad=True):
     G = np.zeros((N, M), order="F") if want_grad else None
     L = _load().oracle_pod_loss_grad(_p(X), N, M, N, _p(wv), int(bool(remove_mean)), int(r), _p(G), N)
     return float(L), G
+
+
+def zsvd(X, k=None, max_sweeps=60):
+    """Complex SVD X = U diag(S) V^H (binary64) by Householder QR and one-sided
+    Jacobi (the per-frequency SVD of SPOD, Alg. 6).  Returns (U (N x k), S, V,
+    sweeps) with the phase rule: the largest |entry| of each v_i is real > 0."""
+    X = np.asfortranarray(np.asarray(X, dtype=np.complex128))
+    N, M = X.shape
+    k = M if k is None else int(k)
+    U = np.zeros((N, max(k, 1)), dtype=np.complex128, order="F")
+    S = np.zeros(M)
+    V = np.zeros((M, M), dtype=np.complex128, order="F")
+    sw = _load().oracle_zsvd(X.ctypes.data, N, M, N, k, U.ctypes.data, N, _p(S), V.ctypes.data, M,
+                             int(max_sweeps))
+    return U[:, :k], S, V, sw
+
+
+def zhouseholder_qr(A):
+    """Complex Householder QR (packed reflectors + R, tau)."""
+    A = np.asfortranarray(np.asarray(A, dtype=np.complex128)).copy(order="F")
+    n, m = A.shape
+    tau = np.zeros(m, dtype=np.complex128)
+    _load().oracle_zhouseholder_qr(A.ctypes.data, n, m, n, tau.ctypes.data)
+    return A, tau

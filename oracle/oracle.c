@@ -413,3 +413,156 @@ double oracle_pod_loss_grad(const double* X, int64_t N, int64_t M, int64_t ldx,
   free(Y); free(U); free(S); free(VT); free(C);
   return L;
 }
+
+/* ========================================================================
+ * Complex (binary64) SVD of a tall matrix, for the per-frequency SVDs of
+ * SPOD (Sec. 2.3, Alg. 6: (1/sqrt(nBlks)) Q_f = U_f S_f V_f^H).  Same route
+ * as the real POD: Householder QR, one-sided Jacobi on R, U = Q [U_r; 0].
+ * ======================================================================== */
+typedef double complex zc;
+#define Z_(i, j) A[(int64_t)(j) * lda + (i)]
+
+/* Householder QR with complex reflectors: H_j = I - tau_j v_j v_j^H,
+ * H_j^H [alpha; x] = [beta; 0] with beta real, beta = -sign(Re alpha)|[alpha; x]|
+ * (sign(0) = +1), tau_j = (beta - alpha) / beta, v_j = [1; x / (alpha - beta)];
+ * A = Q [R; 0] with Q = H_0 H_1 ... H_{m-1}.  A column that is already
+ * [real; 0] gets tau = 0. */
+void oracle_zhouseholder_qr(zc* A, int64_t n, int64_t m, int64_t lda, zc* tau) {
+  for (int64_t j = 0; j < m; ++j) {
+    zc alpha = Z_(j, j);
+    double xx = 0.0;
+    for (int64_t i = j + 1; i < n; ++i) xx += creal(Z_(i, j) * conj(Z_(i, j)));
+    if (xx == 0.0 && cimag(alpha) == 0.0) { tau[j] = 0.0; continue; }
+    double nrm = sqrt(creal(alpha) * creal(alpha) + cimag(alpha) * cimag(alpha) + xx);
+    double beta = (creal(alpha) >= 0.0) ? -nrm : nrm;
+    tau[j] = (beta - alpha) / beta;
+    zc scal = 1.0 / (alpha - beta);
+    for (int64_t i = j + 1; i < n; ++i) Z_(i, j) *= scal;
+    Z_(j, j) = beta;
+    /* apply H_j^H = I - conj(tau) v v^H to the trailing columns */
+#pragma omp parallel for schedule(static)
+    for (int64_t k = j + 1; k < m; ++k) {
+      zc s = Z_(j, k);
+      for (int64_t i = j + 1; i < n; ++i) s += conj(Z_(i, j)) * Z_(i, k);
+      s *= conj(tau[j]);
+      Z_(j, k) -= s;
+      for (int64_t i = j + 1; i < n; ++i) Z_(i, k) -= s * Z_(i, j);
+    }
+  }
+}
+
+/* C := Q C (C is n x k). */
+void oracle_zapply_q(const zc* A, int64_t n, int64_t m, int64_t lda, const zc* tau, zc* C, int64_t k,
+                     int64_t ldc) {
+  for (int64_t j = m - 1; j >= 0; --j) {
+    if (tau[j] == 0.0) continue;
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < k; ++c) {
+      zc* col = C + c * ldc;
+      zc s = col[j];
+      for (int64_t i = j + 1; i < n; ++i) s += conj(Z_(i, j)) * col[i];
+      s *= tau[j];
+      col[j] -= s;
+      for (int64_t i = j + 1; i < n; ++i) col[i] -= s * Z_(i, j);
+    }
+  }
+}
+
+/* One-sided complex Jacobi: for a pair with gamma = a_i^H a_j = |gamma| e^{i phi}
+ * the real rotation of the real case (zeta = (beta - alpha) / (2|gamma|)) acts
+ * on [a_i, e^{-i phi} a_j]:  a_i <- c a_i - s e^{-i phi} a_j,
+ * a_j <- s a_i + c e^{-i phi} a_j, and the same on V.  Cyclic by row;
+ * rotate while |gamma| > n 2^-53 sqrt(alpha beta).  Returns sweeps or -1. */
+int oracle_zjacobi_svd(zc* A, int64_t n, int64_t m, int64_t lda, double* S, zc* V, int64_t ldv,
+                       int max_sweeps) {
+  const double tol = (double)n * ldexp(1.0, -53);
+  for (int64_t j = 0; j < m; ++j)
+    for (int64_t i = 0; i < m; ++i) V[j * ldv + i] = (i == j) ? 1.0 : 0.0;
+  int sweep = 0, converged = 0;
+  while (sweep < max_sweeps && !converged) {
+    int rotated = 0;
+    for (int64_t i = 0; i < m - 1; ++i) {
+      for (int64_t j = i + 1; j < m; ++j) {
+        double alpha = 0.0, beta = 0.0;
+        zc gamma = 0.0;
+        for (int64_t k = 0; k < n; ++k) {
+          alpha += creal(conj(Z_(k, i)) * Z_(k, i));
+          beta += creal(conj(Z_(k, j)) * Z_(k, j));
+          gamma += conj(Z_(k, i)) * Z_(k, j);
+        }
+        double g = cabs(gamma);
+        if (g == 0.0 || g <= tol * sqrt(alpha * beta)) continue;
+        rotated = 1;
+        zc eph = conj(gamma) / g; /* e^{-i phi} */
+        double zeta = (beta - alpha) / (2.0 * g);
+        double t = ((zeta >= 0.0) ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double c = 1.0 / sqrt(1.0 + t * t);
+        double s = c * t;
+        for (int64_t k = 0; k < n; ++k) {
+          zc ai = Z_(k, i), aj = eph * Z_(k, j);
+          Z_(k, i) = c * ai - s * aj;
+          Z_(k, j) = s * ai + c * aj;
+        }
+        for (int64_t k = 0; k < m; ++k) {
+          zc vi = V[i * ldv + k], vj = eph * V[j * ldv + k];
+          V[i * ldv + k] = c * vi - s * vj;
+          V[j * ldv + k] = s * vi + c * vj;
+        }
+      }
+    }
+    ++sweep;
+    if (!rotated) converged = 1;
+  }
+  for (int64_t i = 0; i < m; ++i) {
+    double ss = 0.0;
+    for (int64_t k = 0; k < n; ++k) ss += creal(conj(Z_(k, i)) * Z_(k, i));
+    S[i] = sqrt(ss);
+  }
+  return converged ? sweep : -1;
+}
+
+/* Complex SVD X = U diag(S) V^H of an N x M (N >= M) matrix by QR + Jacobi:
+ * sorted descending (stable), each pair (u_i, v_i) multiplied by the unit
+ * phase that makes the largest-magnitude entry of v_i real and positive
+ * (lowest index on ties).  Outputs U (N x k, first k columns), S (M),
+ * V (M x M).  Zero singular values are not completed (U columns left 0).
+ * Returns Jacobi sweeps or -1. */
+int oracle_zsvd(const zc* X, int64_t N, int64_t M, int64_t ldx, int64_t k, zc* U, int64_t ldu,
+                double* S, zc* V, int64_t ldv, int max_sweeps) {
+  zc* Y = (zc*)malloc(sizeof(zc) * N * M);
+  zc* tau = (zc*)malloc(sizeof(zc) * M);
+  zc* R = (zc*)malloc(sizeof(zc) * M * M);
+  zc* Vw = (zc*)malloc(sizeof(zc) * M * M);
+  double* Sw = (double*)malloc(sizeof(double) * M);
+  int64_t* perm = (int64_t*)malloc(sizeof(int64_t) * M);
+  for (int64_t j = 0; j < M; ++j) memcpy(Y + j * N, X + j * ldx, sizeof(zc) * N);
+  oracle_zhouseholder_qr(Y, N, M, N, tau);
+  for (int64_t j = 0; j < M; ++j)
+    for (int64_t i = 0; i < M; ++i) R[j * M + i] = (i <= j) ? Y[j * N + i] : 0.0;
+  int sw = oracle_zjacobi_svd(R, M, M, M, Sw, Vw, M, max_sweeps);
+  for (int64_t i = 0; i < M; ++i) perm[i] = i;
+  for (int64_t i = 1; i < M; ++i) {
+    int64_t p = perm[i], q = i;
+    while (q > 0 && Sw[perm[q - 1]] < Sw[p]) { perm[q] = perm[q - 1]; --q; }
+    perm[q] = p;
+  }
+  for (int64_t c = 0; c < M; ++c) {
+    int64_t p = perm[c];
+    S[c] = Sw[p];
+    int64_t kmax = 0;
+    double vmax = -1.0;
+    for (int64_t q = 0; q < M; ++q) {
+      double a = cabs(Vw[p * M + q]);
+      if (a > vmax) { vmax = a; kmax = q; }
+    }
+    zc ph = (vmax > 0.0) ? conj(Vw[p * M + kmax]) / vmax : 1.0;
+    for (int64_t q = 0; q < M; ++q) V[c * ldv + q] = Vw[p * M + q] * ph;
+    if (c < k) {
+      zc* col = U + c * ldu;
+      for (int64_t i = 0; i < N; ++i) col[i] = (i < M && Sw[p] > 0.0) ? R[p * M + i] * ph / Sw[p] : 0.0;
+    }
+  }
+  oracle_zapply_q(Y, N, M, N, tau, U, k, ldu);
+  free(Y); free(tau); free(R); free(Vw); free(Sw); free(perm);
+  return sw;
+}

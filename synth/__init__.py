@@ -173,3 +173,78 @@ def known_spectrum_torch(N: int, M: int, device, s=None, weights: bool = True, s
     XT = Y.T.contiguous().to(dtype)
     del Y
     return XT, w, np.asarray(s, dtype=np.float64)
+
+
+# ----------------------------------------------------------------------------
+# complex per-frequency matrices (SPOD bins)
+# ----------------------------------------------------------------------------
+
+def unitary_columns(N: int, M: int, seed: int) -> np.ndarray:
+    """Seeded N x M matrix with orthonormal complex columns (library QR of a
+    complex Gaussian, phases of R's diagonal moved into Q)."""
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((N, M)) + 1j * rng.standard_normal((N, M))
+    Q, R = np.linalg.qr(G)
+    d = np.diag(R)
+    return Q * (d / np.abs(d))[None, :]
+
+
+def complex_known_spectrum(N: int, M: int, s=None, seeds=(81, 82), dtype=np.complex128):
+    """X = Q1 diag(s) Q2^H with seeded orthonormal complex Q1 (N x M) and
+    unitary Q2 (M x M): singular values s exactly."""
+    if s is None:
+        s = spectrum(M)
+    Q1 = unitary_columns(N, M, seeds[0])
+    Q2 = unitary_columns(M, M, seeds[1])
+    X = (Q1 * np.asarray(s)[None, :]) @ Q2.conj().T
+    return np.asfortranarray(X.astype(dtype)), np.asarray(s, dtype=np.float64)
+
+
+def spod_bin_sizes(n_bins: int, seed: int, n_lo: int = 1 << 16, n_hi: int = 1 << 20,
+                   nb_lo: int = 16, nb_hi: int = 128):
+    """Per-bin sizes of the batched SPOD workload: N_f log-uniform in
+    [n_lo, n_hi], Nb_f uniform integers in [nb_lo, nb_hi]."""
+    rng = np.random.default_rng(seed)
+    N = np.round(np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=n_bins))).astype(np.int64)
+    Nb = rng.integers(nb_lo, nb_hi + 1, size=n_bins).astype(np.int64)
+    return N, Nb
+
+
+def spod_bin(N: int, Nb: int, seed: int, n_waves: int = 4, noise: float = 1e-3, dtype=np.complex64):
+    """One frequency bin's matrix of block Fourier coefficients of a
+    traveling-wave field (numpy, Fortran order): a traveling wave
+    a sin(k x - w t) seen through windowed blocks contributes, at its own
+    frequency, a spatial complex exponential exp(i k x) whose coefficient in
+    block b carries the phase of that block's start time, so the bin is
+    sum_j a_j exp(i k_j x) exp(i phi_jb) + complex noise, scaled by
+    1/sqrt(Nb) like the SPOD matrix.  Phases and noise are seeded."""
+    rng = np.random.default_rng(seed)
+    x = 2.0 * np.pi * np.arange(N, dtype=np.float64) / N
+    k = 1 + rng.permutation(min(N // 2 - 1, 4096))[:n_waves]
+    a = 2.0 ** (-np.arange(n_waves, dtype=np.float64))
+    Fx = np.exp(1j * np.outer(x, k))                       # N x J
+    Ph = np.exp(1j * rng.uniform(0.0, 2.0 * np.pi, size=(n_waves, Nb))) * a[:, None]
+    X = Fx @ Ph
+    X += noise * (rng.standard_normal((N, Nb)) + 1j * rng.standard_normal((N, Nb))) / math.sqrt(2.0)
+    X /= math.sqrt(Nb)
+    return np.asfortranarray(X.astype(dtype))
+
+
+def spod_bin_torch(N: int, Nb: int, seed: int, device, n_waves: int = 4, noise: float = 1e-3):
+    """Device-side :func:`spod_bin` (complex64); returns XT of shape (Nb, N)
+    so that XT.T is the column-major N x Nb matrix."""
+    import torch
+    rng = np.random.default_rng(seed)
+    k = 1 + rng.permutation(min(N // 2 - 1, 4096))[:n_waves]
+    a = 2.0 ** (-np.arange(n_waves, dtype=np.float64))
+    Ph = np.exp(1j * rng.uniform(0.0, 2.0 * np.pi, size=(n_waves, Nb))) * a[:, None]
+    x = 2.0 * math.pi * torch.arange(N, dtype=torch.float64, device=device) / N
+    kk = torch.tensor(k, dtype=torch.float64, device=device)
+    Fx = torch.exp(1j * torch.outer(x, kk))
+    X = Fx @ torch.tensor(Ph, dtype=torch.complex128, device=device)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    X += noise * torch.complex(torch.randn((N, Nb), dtype=torch.float64, device=device, generator=gen),
+                               torch.randn((N, Nb), dtype=torch.float64, device=device, generator=gen)) / math.sqrt(2.0)
+    X /= math.sqrt(Nb)
+    return X.T.contiguous().to(torch.complex64)

@@ -24,6 +24,11 @@ MUTATIONS = {
     "truncation_strict": ("if (acc / total >= energy)", "if (acc / total > energy)"),
     "transposed_vt": ("VT[k * ldvt + i] = V[i * M + k];", "VT[k * ldvt + i] = V[k * M + i];"),
     "grad_factor": ("double g = 2.0 * (Y[m * N + n] - p) * swn;", "double g = 1.0 * (Y[m * N + n] - p) * swn;"),
+    "zqr_missing_conj": ("for (int64_t i = j + 1; i < n; ++i) s += conj(Z_(i, j)) * Z_(i, k);",
+                         "for (int64_t i = j + 1; i < n; ++i) s += Z_(i, j) * Z_(i, k);"),
+    "zjacobi_phase": ("zc eph = conj(gamma) / g; /* e^{-i phi} */", "zc eph = gamma / g; /* e^{-i phi} */"),
+    "zsvd_phase_rule": ("zc ph = (vmax > 0.0) ? conj(Vw[p * M + kmax]) / vmax : 1.0;",
+                        "zc ph = (vmax > 0.0) ? Vw[p * M + kmax] / vmax : 1.0;"),
     "grad_weight_missing": ("double g = 2.0 * (Y[m * N + n] - p) * swn;", "double g = 2.0 * (Y[m * N + n] - p);"),
 }
 

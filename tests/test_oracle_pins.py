@@ -316,3 +316,65 @@ def test_loss_gradient_vanishes_for_rank_r():
     L, G = oracle.pod_loss_grad(X, r)
     assert abs(L) < 1e-24 * np.linalg.norm(X) ** 2 + 1e-26
     assert np.abs(G).max() < 1e-12 * np.abs(X).max()
+
+
+# ---------------------------------------------------------------------------
+# complex SVD (per-frequency SVDs of SPOD)
+# ---------------------------------------------------------------------------
+
+def test_zqr_reflector_convention():
+    # H^H [alpha; x] = [beta; 0] with beta real and opposite in sign to Re(alpha)
+    A = np.array([[3.0 + 4.0j], [0.0 + 0.0j], [12.0 + 0.0j]])
+    packed, tau = oracle.zhouseholder_qr(A)
+    assert packed[0, 0].imag == 0.0
+    assert packed[0, 0].real == pytest.approx(-13.0, abs=1e-14)
+    assert tau[0] == pytest.approx((-13.0 - (3.0 + 4.0j)) / -13.0, abs=1e-15)
+
+
+def test_zsvd_closed_form_spectrum():
+    N, M = 600, 24
+    X, s = synth.complex_known_spectrum(N, M, seeds=(91, 92))
+    U, S, V, sw = oracle.zsvd(X)
+    assert sw > 0
+    assert np.max(np.abs(S - s)) <= 1e-13 * s[0]
+    nX = np.linalg.norm(X)
+    assert np.linalg.norm(X - (U * S) @ V.conj().T) / nX <= 1e-13
+    assert np.linalg.norm(U.conj().T @ U - np.eye(M)) <= 1e-12
+    assert np.linalg.norm(V.conj().T @ V - np.eye(M)) <= 1e-12
+    # phase rule: the largest |entry| of each v_i is real and positive
+    for i in range(M):
+        k = int(np.argmax(np.abs(V[:, i])))
+        assert abs(V[k, i].imag) <= 1e-15 and V[k, i].real > 0
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 5])
+def test_zsvd_brute_force_tiny(M):
+    rng = _rng(200 + M)
+    X = rng.standard_normal((11, M)) + 1j * rng.standard_normal((11, M))
+    _, S, _, _ = oracle.zsvd(X)
+    lam = np.linalg.eigvalsh(X.conj().T @ X)[::-1]
+    assert np.allclose(S, np.sqrt(np.maximum(lam, 0.0)), rtol=1e-12, atol=1e-13 * np.sqrt(lam[0]))
+    if M == 2:
+        G = X.conj().T @ X     # Hermitian 2x2: (a + c)/2 +- sqrt(((a - c)/2)^2 + |b|^2)
+        l1, l2 = cf.sym2x2_eigs(G[0, 0].real, abs(G[0, 1]), G[1, 1].real)
+        assert S[0] == pytest.approx(math.sqrt(l1), rel=1e-13)
+        assert S[1] == pytest.approx(math.sqrt(l2), rel=1e-12)
+
+
+def test_zsvd_of_real_input_matches_real_oracle():
+    X = _rng(17).standard_normal((80, 9))
+    Uz, Sz, Vz, _ = oracle.zsvd(X.astype(np.complex128))
+    Ur, Sr, Vr, _ = oracle.svd(X)
+    assert np.allclose(Sz, Sr, rtol=1e-13)
+    # same phase rule: for real data the factors coincide
+    assert np.allclose(Vz.real, Vr, atol=1e-12) and np.abs(Vz.imag).max() < 1e-12
+    assert np.allclose(Uz.real, Ur, atol=1e-12) and np.abs(Uz.imag).max() < 1e-12
+
+
+def test_zsvd_wave_bin_has_wave_rank():
+    # a bin of 4 coherent waves plus 1e-3 noise: 4 singular values stand out
+    X = synth.spod_bin(4096, 20, seed=5).astype(np.complex128)
+    _, S, _, _ = oracle.zsvd(X)
+    assert S[3] > 100 * S[4]
+    _, S0, _, _ = oracle.zsvd(synth.spod_bin(4096, 20, seed=5, noise=0.0).astype(np.complex128))
+    assert np.all(S0[4:] <= 1e-6 * S0[0])
