@@ -37,9 +37,10 @@ MUTATIONS = {
 def test_pins_catch_planted_mistake(name, tmp_path):
     old, new = MUTATIONS[name]
     src = open(SRC).read()
-    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    # the first occurrence is mutated (the real routines precede the complex ones)
+    assert src.count(old) >= 1, f"mutation anchor for {name} not found"
     mutated = tmp_path / "oracle_mut.c"
-    mutated.write_text(src.replace(old, new))
+    mutated.write_text(src.replace(old, new, 1))
     lib = tmp_path / "liboracle_mut.so"
     subprocess.run(["gcc", "-O2", "-std=c99", "-fopenmp", "-fPIC", "-shared", "-o", str(lib),
                     str(mutated), "-lm"], check=True)
