@@ -180,6 +180,47 @@ pylom_status pylom_svd_small(const double* R, int64_t M, int64_t ldr, double* U,
                              void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Batched complex SVDs -- the per-frequency SVDs of SPOD (Sec. 2.3, Alg. 6:
+ * (1/sqrt(nBlks)) Q_f = U_f S_f V_f^H for every frequency bin f), all bins
+ * in one cooperative persistent launch.  Each bin: TSQR with complex
+ * Householder leaves and a last-arriver tree (Alg. 1), one-sided Jacobi SVD
+ * of its R (Eq. svdqr2), modes U_f = Q_f U_r (Eq. svdqr3).
+ * Three steps, so the launch can be captured in a CUDA graph:
+ *   plan  (host only): bin sizes N[f] x Nb[f] (1 <= Nb <= 128, N >= Nb),
+ *         optional per-bin leaf heights (NULL or <= 0: built-in choice, an
+ *         autotuner may supply them), kmodes (0..32 modes returned per bin,
+ *         capped at Nb), prec: PYLOM_PREC_FP64 (complex128 leaves) or
+ *         PYLOM_PREC_MIXED_3XTF32 (complex64 leaves with compensated FP32
+ *         sums; tree, Jacobi and R always binary64).  Returns an opaque plan
+ *         and the workspace size.
+ *   bind  Q[f]: device pointer (host array of them) to bin f's complex64
+ *         N x Nb matrix (column-major, ldq[f] >= N), not modified; U[f]:
+ *         device complex64 N x min(kmodes, Nb) output (ldu[f] >= N); writes
+ *         the plan's tables into the workspace and synchronises `stream`.
+ *         Not capturable; call once per set of buffers.
+ *   run   S: device doubles, sum_f Nb[f], bin f at offset
+ *         pylom_svd_batched_plan_info(plan, f, 2), descending per bin;
+ *         U[f] columns carry the phase rule (the largest |entry| of each
+ *         right vector real and positive).  Capturable (memsets + one
+ *         cooperative kernel, no host synchronisation).
+ * Device-side conditions (non-finite input, Jacobi not converged, a bounded
+ * wait that expired) go to the workspace header (pylom_workspace_status).
+ * ------------------------------------------------------------------------ */
+typedef struct pylom_batched_plan pylom_batched_plan;
+pylom_status pylom_svd_batched_plan(int nbins, const int64_t* N, const int64_t* Nb,
+                                    const int64_t* leaf_rows, int64_t kmodes, int prec,
+                                    pylom_batched_plan** plan, size_t* ws_bytes);
+pylom_status pylom_svd_batched_bind(pylom_batched_plan* plan, const void* const* Q, const int64_t* ldq,
+                                    void* const* U, const int64_t* ldu, void* ws, size_t ws_bytes,
+                                    void* stream);
+pylom_status pylom_svd_batched_run(const pylom_batched_plan* plan, void* ws, double* S, int max_sweeps,
+                                   void* stream);
+/* what: 0 leaf height, 1 leaf count, 2 offset of the bin's S, 3 grid size,
+ * 4 number of leaf items; -1 on a bad argument. */
+int64_t pylom_svd_batched_plan_info(const pylom_batched_plan* plan, int bin, int what);
+void pylom_svd_batched_plan_destroy(pylom_batched_plan* plan);
+
+/* ------------------------------------------------------------------------
  * pylom_matmul -- local product of Alg. 4 (matmul_paral) on one device:
  * C = op(A) B, op(A) = A (m x k, lda >= m) or A^T (A stored k x m,
  * lda >= k); B k x n (ldb >= k); C m x n (ldc >= m).  binary64 on the FP64

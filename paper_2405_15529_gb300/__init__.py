@@ -37,6 +37,8 @@ EXPORTS = (
     "pylom_matmul", "pylom_profile_begin", "pylom_profile_end",
     "pylom_probe_scratch_bytes", "pylom_probe_fp64_peak", "pylom_svd_small_noalloc",
     "pylom_pod_backward_workspace_size", "pylom_pod_backward",
+    "pylom_svd_batched_plan", "pylom_svd_batched_bind", "pylom_svd_batched_run",
+    "pylom_svd_batched_plan_info", "pylom_svd_batched_plan_destroy",
 )
 PROFILE_PHASES = ("leaf_qr_tree", "svd_small", "down_pass", "modes")
 
@@ -96,6 +98,18 @@ def load_library(path: str = LIB_PATH):
     lib.pylom_pod_backward.restype = _int
     lib.pylom_pod_backward.argtypes = [_vp, _sz, _i64, _i64, _i64, _i64, _i64, _vp, _int, _int, _vp, _vp,
                                        _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, _int, _vp, _sz, _vp]
+    lib.pylom_svd_batched_plan.restype = _int
+    lib.pylom_svd_batched_plan.argtypes = [_int, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                           _i64, _int, ctypes.POINTER(_vp), ctypes.POINTER(_sz)]
+    lib.pylom_svd_batched_bind.restype = _int
+    lib.pylom_svd_batched_bind.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_i64), ctypes.POINTER(_vp),
+                                           ctypes.POINTER(_i64), _vp, _sz, _vp]
+    lib.pylom_svd_batched_run.restype = _int
+    lib.pylom_svd_batched_run.argtypes = [_vp, _vp, _vp, _int, _vp]
+    lib.pylom_svd_batched_plan_info.restype = _i64
+    lib.pylom_svd_batched_plan_info.argtypes = [_vp, _int, _int]
+    lib.pylom_svd_batched_plan_destroy.restype = None
+    lib.pylom_svd_batched_plan_destroy.argtypes = [_vp]
     lib.pylom_svd_small_noalloc.restype = _int
     lib.pylom_svd_small_noalloc.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _int, _vp, _vp]
     lib.pylom_probe_scratch_bytes.restype = _sz
@@ -409,3 +423,85 @@ def pod_autograd(X, r, w=None, remove_mean=False, mode_kind=MODES_ORTHONORMAL, l
     if _PodFn is None:
         _PodFn = _make_pod_function()
     return _PodFn.apply(X, w, int(r), bool(remove_mean), int(mode_kind), int(leaf_rows))
+
+
+class BatchedSVD:
+    """Batched complex SVDs (the per-frequency SVDs of SPOD) in one
+    persistent launch.  Q: list of column-major complex64 CUDA tensors
+    (N_f x Nb_f).  After run(): S[f] (Nb_f,) descending, U[f] (N_f x k_f).
+    capture() records run() in a CUDA graph; replay() re-runs it."""
+
+    def __init__(self, Q, kmodes=8, prec=PREC_MIXED_3XTF32, leaf_rows=None, max_sweeps=60):
+        torch = _torch()
+        lib = load_library()
+        self.lib = lib
+        self.Q = [_colmajor(q) for q in Q]
+        for q in self.Q:
+            if q.dtype != torch.complex64:
+                raise TypeError("bins must be complex64")
+        n = len(self.Q)
+        self.N = [int(q.shape[0]) for q in self.Q]
+        self.Nb = [int(q.shape[1]) for q in self.Q]
+        Na = (_i64 * n)(*self.N)
+        Nba = (_i64 * n)(*self.Nb)
+        lr = None
+        if leaf_rows is not None:
+            lr = (_i64 * n)(*[int(x) for x in leaf_rows])
+        plan = _vp()
+        wsb = _sz(0)
+        _raise(lib.pylom_svd_batched_plan(n, Na, Nba, lr, int(kmodes), int(prec), ctypes.byref(plan),
+                                          ctypes.byref(wsb)), "pylom_svd_batched_plan")
+        self.plan = plan
+        self.max_sweeps = int(max_sweeps)
+        dev = self.Q[0].device
+        self.ws = torch.empty(int(wsb.value), dtype=torch.uint8, device=dev)
+        self.S_all = torch.zeros(sum(self.Nb), dtype=torch.float64, device=dev)
+        self.k = [min(int(kmodes), nb) for nb in self.Nb]
+        self.U = [empty_colmajor(N_f, max(k, 1), torch.complex64, dev) for N_f, k in zip(self.N, self.k)]
+        qp = (_vp * n)(*[q.data_ptr() for q in self.Q])
+        ldq = (_i64 * n)(*[_ld(q) for q in self.Q])
+        up = (_vp * n)(*[u.data_ptr() for u in self.U])
+        ldu = (_i64 * n)(*[_ld(u) for u in self.U])
+        _raise(lib.pylom_svd_batched_bind(plan, qp, ldq, up, ldu, _dptr(self.ws), self.ws.numel(),
+                                          _stream(None)), "pylom_svd_batched_bind")
+        self.graph = None
+
+    def info(self, f, what):
+        return int(self.lib.pylom_svd_batched_plan_info(self.plan, int(f), int(what)))
+
+    @property
+    def S(self):
+        return [self.S_all[self.info(f, 2): self.info(f, 2) + nb] for f, nb in enumerate(self.Nb)]
+
+    @property
+    def modes(self):
+        return [u[:, :k] for u, k in zip(self.U, self.k)]
+
+    def run(self, stream=None):
+        _raise(self.lib.pylom_svd_batched_run(self.plan, _dptr(self.ws), _dptr(self.S_all), self.max_sweeps,
+                                              _stream(stream)), "pylom_svd_batched_run")
+
+    def status(self, stream=None):
+        st, _, _ = workspace_status(self.ws, stream)
+        return st
+
+    def capture(self):
+        torch = _torch()
+        self.run()                       # warm-up outside capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run(torch.cuda.current_stream())
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
+    def __del__(self):
+        try:
+            if getattr(self, "plan", None):
+                self.lib.pylom_svd_batched_plan_destroy(self.plan)
+                self.plan = None
+        except Exception:
+            pass

@@ -1,0 +1,105 @@
+"""Autotuner of the batched complex SVD: the TSQR leaf height of each bin.
+
+The leaf height trades the leaf QR's memory traffic (a taller leaf streams
+its trailing columns from HBM once per reflector) against the binary64 tree
+(P - 1 merges of (8/3) Nb^3 real flops each).  For every (Nb class, N class)
+the tuner times a small batch of seeded sample bins with each candidate
+height through the library's own batched launch and keeps the fastest.
+Results are cached in JSON, keyed by GPU name, precision and class; the cache
+file is a runtime artifact (PYLOM_TUNE_CACHE overrides its path).
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import time
+
+import paper_2405_15529_gb300 as pg
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+CACHE = os.environ.get("PYLOM_TUNE_CACHE", os.path.join(_HERE, "tune_cache.json"))
+
+
+def _classes(N: int, Nb: int):
+    nb_c = 1 << max(0, math.ceil(math.log2(max(Nb, 1))))
+    n_c = int(math.floor(math.log2(max(N, 1))))
+    return nb_c, n_c
+
+
+def _key(gpu: str, prec: int, nb_c: int, n_c: int) -> str:
+    return f"{gpu}|prec{prec}|nb{nb_c}|n2^{n_c}"
+
+
+def _load():
+    try:
+        with open(CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _save(d):
+    tmp = CACHE + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, CACHE)
+
+
+def candidates(N: int, Nb: int):
+    c = sorted({max(Nb, h) for h in (256, 512, 1024, 2048, 4096, 8192, 16384)})
+    return [h for h in c if h <= N]
+
+
+def time_leaf_rows(N: int, Nb: int, prec: int, h: int, nbins: int = 8, reps: int = 3, seed: int = 0) -> float:
+    """Median seconds of one batched run over `nbins` seeded N x Nb bins."""
+    import torch
+    import synth
+    Q = [synth.spod_bin_torch(N, Nb, seed + i, device="cuda").t() for i in range(nbins)]
+    b = pg.BatchedSVD(Q, kmodes=min(8, Nb), prec=prec, leaf_rows=[h] * nbins)
+    b.run()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.run()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) * 1e-3)
+    st = b.status()
+    if st != pg.OK:
+        raise pg.PylomError(st, "autotuner sample run")
+    ts.sort()
+    return ts[len(ts) // 2]
+
+
+def tune_class(N: int, Nb: int, prec: int) -> int:
+    best, best_t = None, float("inf")
+    for h in candidates(N, Nb):
+        t = time_leaf_rows(N, Nb, prec, h)
+        if t < best_t:
+            best, best_t = h, t
+    return best
+
+
+def leaf_rows_for(Ns, Nbs, prec: int, tune: bool = False):
+    """Leaf heights for a batch (from the cache; missing classes are tuned
+    when `tune`, else left to the library's built-in choice, 0)."""
+    import torch
+    gpu = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+    cache = _load()
+    out = []
+    dirty = False
+    for N, Nb in zip(Ns, Nbs):
+        nb_c, n_c = _classes(int(N), int(Nb))
+        k = _key(gpu, prec, nb_c, n_c)
+        if k not in cache and tune:
+            cache[k] = tune_class(1 << n_c, nb_c, prec)
+            dirty = True
+        h = int(cache.get(k, 0))
+        out.append(max(h, int(Nb)) if h else 0)
+    if dirty:
+        _save(cache)
+    return out
