@@ -20,7 +20,8 @@ extern "C" {
 #endif
 
 /* Runs a throughput loop of independent FP64 MMAs (kind 0: mma.sync
- * m8n8k4 f64) or FP64 FMAs (kind 1) over every SM of the current device on
+ * m8n8k4 f64), FP64 FMAs (kind 1) or FP32 FMAs (kind 2) over every SM of
+ * the current device on
  * `stream`, synchronises, and writes to HOST memory the achieved TFLOP/s.
  * scratch: device buffer of >= pylom_probe_scratch_bytes() bytes (results
  * are stored there so the loop is not optimised away). */

@@ -177,13 +177,13 @@ def profile_end():
 
 
 def probe_fp64_peak(kind: str = "mma") -> float:
-    """Measured FP64 TFLOP/s of this GPU: kind 'mma' (tensor pipe,
-    mma.sync.m8n8k4.f64) or 'fma' (scalar FP64 FMA)."""
+    """Measured TFLOP/s of this GPU: kind 'mma' (FP64 tensor pipe,
+    mma.sync.m8n8k4.f64), 'fma' (scalar FP64 FMA) or 'ffma' (FP32 FMA)."""
     torch = _torch()
     lib = load_library()
     scratch = torch.empty(lib.pylom_probe_scratch_bytes(), dtype=torch.uint8, device="cuda")
     out = ctypes.c_double(0.0)
-    st = lib.pylom_probe_fp64_peak(0 if kind == "mma" else 1, _dptr(scratch), ctypes.byref(out),
+    st = lib.pylom_probe_fp64_peak({"mma": 0, "fma": 1, "ffma": 2}[kind], _dptr(scratch), ctypes.byref(out),
                                    _stream(None))
     _raise(st, "pylom_probe_fp64_peak")
     return float(out.value)

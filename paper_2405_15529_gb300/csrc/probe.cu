@@ -40,6 +40,20 @@ __global__ void __launch_bounds__(kProbeThreads) probe_dfma_kernel(double* out, 
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+__global__ void __launch_bounds__(kProbeThreads) probe_ffma_kernel(double* out, float a, float b) {
+  float x[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) x[q] = threadIdx.x + q;
+  for (int it = 0; it < kIters; ++it) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = fmaf(x[q], a, b);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s += x[q];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace
 
 extern "C" size_t pylom_probe_scratch_bytes(void) {
@@ -47,7 +61,7 @@ extern "C" size_t pylom_probe_scratch_bytes(void) {
 }
 
 extern "C" pylom_status pylom_probe_fp64_peak(int kind, void* scratch, double* tflops, void* stream) {
-  if (!scratch || !tflops || (kind != 0 && kind != 1)) return PYLOM_ERR_ARG;
+  if (!scratch || !tflops || kind < 0 || kind > 2) return PYLOM_ERR_ARG;
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return PYLOM_ERR_CUDA;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PYLOM_ERR_CUDA;
@@ -61,15 +75,17 @@ extern "C" pylom_status pylom_probe_fp64_peak(int kind, void* scratch, double* t
     cudaEventRecord(e0, st);
     if (kind == 0)
       probe_dmma_kernel<<<blocks, kProbeThreads, 0, st>>>((double*)scratch, 0.999, 1e-3);
-    else
+    else if (kind == 1)
       probe_dfma_kernel<<<blocks, kProbeThreads, 0, st>>>((double*)scratch, 0.999, 1e-3);
+    else
+      probe_ffma_kernel<<<blocks, kProbeThreads, 0, st>>>((double*)scratch, 0.999f, 1e-3f);
     cudaEventRecord(e1, st);
     if (cudaEventSynchronize(e1) != cudaSuccess) return PYLOM_ERR_CUDA;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     const double threads = (double)blocks * kProbeThreads;
     const double flops = (kind == 0) ? 2.0 * 8 * 8 * 4 * 4.0 * (kIters / 4) * (threads / 32.0)
-                                     : 2.0 * 8 * kIters * threads;
+                                     : 2.0 * 8 * kIters * threads;   // FMA kinds: 8 chains x kIters
     const double tf = flops / (ms * 1e-3) / 1e12;
     if (rep > 0 && tf > best) best = tf;
   }
