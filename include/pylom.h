@@ -52,8 +52,15 @@ typedef enum {
 
 typedef enum { PYLOM_F32 = 0, PYLOM_F64 = 1, PYLOM_C64 = 2, PYLOM_C128 = 3 } pylom_dtype;
 
-/* Arithmetic of the hot path.  FP64: every step in binary64 (trailing
- * updates and the modes product on the FP64 tensor pipe, mma.sync.m8n8k4). */
+/* Arithmetic of the hot path.
+ * FP64: every step in binary64 (trailing updates and the modes product on
+ *   the FP64 tensor pipe, mma.sync.m8n8k4).
+ * MIXED_3XTF32: FP32 leaf working copy; panel sums compensated in FP32 and
+ *   reduced in FP64; the leaves' block-reflector products (trailing updates
+ *   and U = Q [B; 0]) on the tcgen05 tensor cores in 3xTF32 (each FP32
+ *   operand split into a TF32 high part and an FP32 remainder, three MMAs,
+ *   FP32 accumulation in tensor memory); the tree merges, the small SVD of R,
+ *   the mean and the top-down pass stay in binary64. */
 typedef enum { PYLOM_PREC_FP64 = 0, PYLOM_PREC_MIXED_3XTF32 = 1 } pylom_prec;
 
 /* Which left vectors pylom_pod returns (only differs when w != NULL).
@@ -99,8 +106,9 @@ pylom_status pylom_workspace_status(const void* ws, void* stream, int64_t* r, in
  *  r_max        1 <= r_max <= M: the columns U has room for.
  *  mode_kind    pylom_mode_kind (see above).
  *  leaf_rows    TSQR leaf height hint b (0 = automatic; else b >= M).
- *  U      out  N x r_max, ldu >= N, binary64: the first r columns receive
- *              the modes, the rest are left untouched.
+ *  U      out  N x r_max, ldu >= N: the first r columns receive the
+ *              modes, the rest are left untouched.  Element type: binary64
+ *              for PYLOM_PREC_FP64, binary32 for PYLOM_PREC_MIXED_3XTF32.
  *  S      out  M singular values, descending.
  *  VT     out  M x M, ldvt >= M: row i is v_i^T, the temporal coefficients
  *              of mode i (Sec. 3.1).  Each pair (u_i, v_i) is signed so that
@@ -109,7 +117,7 @@ pylom_status pylom_workspace_status(const void* ws, void* stream, int64_t* r, in
  *  mean   out  N temporal means (zeros if !remove_mean), or NULL.
  *  r_out  out  device int64: the chosen r, or NULL (also readable through
  *              pylom_workspace_status).
- *  prec         pylom_prec.  This build implements PYLOM_PREC_FP64.
+ *  prec         pylom_prec (both implemented).
  *  ws, ws_bytes device workspace of at least pylom_pod_workspace_size().
  * ------------------------------------------------------------------------ */
 size_t pylom_pod_workspace_size(int64_t N, int64_t M, int64_t leaf_rows, int64_t r_max,
@@ -117,7 +125,7 @@ size_t pylom_pod_workspace_size(int64_t N, int64_t M, int64_t leaf_rows, int64_t
 pylom_status pylom_pod(const void* X, int64_t N, int64_t M, int64_t ldx, int xtype,
                        const double* w, int remove_mean, double energy, int64_t r_max,
                        int mode_kind, int64_t leaf_rows,
-                       double* U, int64_t ldu, double* S, double* VT, int64_t ldvt,
+                       void* U, int64_t ldu, double* S, double* VT, int64_t ldvt,
                        double* mean, int64_t* r_out, int prec,
                        void* ws, size_t ws_bytes, void* stream);
 
@@ -129,9 +137,9 @@ pylom_status pylom_pod(const void* X, int64_t N, int64_t M, int64_t ldx, int xty
  * tree reflectors that the forward call left in its workspace (Q^T dU by
  * the leaf reflectors and a bottom-up tree pass; Q [B; 0] by the top-down
  * pass); the square SVD adjoint of R runs in binary64 on M x M matrices.
- *  fwd_ws, fwd_ws_bytes  the workspace of the pylom_pod call being
- *                        differentiated, unchanged since (same N, M,
- *                        leaf_rows, r_max, w, remove_mean, mode_kind).
+ *  fwd_ws, fwd_ws_bytes  the workspace of the PYLOM_PREC_FP64 pylom_pod
+ *                        call being differentiated, unchanged since (same
+ *                        N, M, leaf_rows, r_max, w, remove_mean, mode_kind).
  *  r       number of modes whose cotangent dU holds (0 <= r <= r_max).
  *  S, VT   that call's singular values and right vectors (ldvt >= M).
  *  dU      N x r (lddu >= N) or NULL; dS: M or NULL; dVT: M x M or NULL.

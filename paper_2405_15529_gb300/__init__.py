@@ -243,7 +243,7 @@ def pod(X, w=None, remove_mean=True, energy=0.0, r_max=None, mode_kind=MODES_ORT
     if workspace is None or workspace.numel() < need:
         workspace = torch.empty(need, dtype=torch.uint8, device=dev)
     if out is None:
-        U = empty_colmajor(N, r_max, torch.float64, dev)
+        U = empty_colmajor(N, r_max, torch.float32 if prec == PREC_MIXED_3XTF32 else torch.float64, dev)
         S = torch.empty(M, dtype=torch.float64, device=dev)
         VT = empty_colmajor(M, M, torch.float64, dev)
         mean = torch.empty(N, dtype=torch.float64, device=dev)

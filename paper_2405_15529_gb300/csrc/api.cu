@@ -100,22 +100,25 @@ extern "C" pylom_status pylom_workspace_status(const void* ws, void* stream, int
 // POD (Alg. 2 + Alg. 1 + Eqs. svdqr1-svdqr3)
 // ---------------------------------------------------------------------------
 
-static size_t pod_bytes(int64_t N, int64_t M, int64_t P, int64_t r_max) {
-  return sizeof(WsHeader) + tsqr_state_bytes(N, M, P, r_max) + svd_state_bytes(M) +
-         align256(sizeof(double) * (size_t)M * M);
+// Workspace of pylom_pod: header | TSQR state | Jacobi state | U_R |
+// (mixed only) FP32 working copy and 32-column panel factors.
+static size_t pod_bytes(int64_t N, int64_t M, int64_t P, int64_t r_max, int prec = PYLOM_PREC_FP64) {
+  const bool mixed = prec == PYLOM_PREC_MIXED_3XTF32;
+  return sizeof(WsHeader) + tsqr_state_bytes(N, M, P, r_max, !mixed) + svd_state_bytes(M) +
+         align256(sizeof(double) * (size_t)M * M) + (mixed ? mixed_extra_bytes(N, M, P) : 0);
 }
 
 extern "C" size_t pylom_pod_workspace_size(int64_t N, int64_t M, int64_t leaf_rows, int64_t r_max,
                                            int xtype, int prec) {
   if (!tall_shape_ok(N, M, leaf_rows) || r_max < 1 || r_max > M) return 0;
   if (xtype != PYLOM_F32 && xtype != PYLOM_F64) return 0;
-  if (prec != PYLOM_PREC_FP64) return 0;
-  return pod_bytes(N, M, leaves_of(N, M, leaf_rows), r_max);
+  if (prec != PYLOM_PREC_FP64 && prec != PYLOM_PREC_MIXED_3XTF32) return 0;
+  return pod_bytes(N, M, leaves_of(N, M, leaf_rows), r_max, prec);
 }
 
 extern "C" pylom_status pylom_pod(const void* X, int64_t N, int64_t M, int64_t ldx, int xtype,
                                   const double* w, int remove_mean, double energy, int64_t r_max,
-                                  int mode_kind, int64_t leaf_rows, double* U, int64_t ldu,
+                                  int mode_kind, int64_t leaf_rows, void* U, int64_t ldu,
                                   double* S, double* VT, int64_t ldvt, double* mean,
                                   int64_t* r_out, int prec, void* ws, size_t ws_bytes,
                                   void* stream) {
@@ -134,10 +137,9 @@ extern "C" pylom_status pylom_pod(const void* X, int64_t N, int64_t M, int64_t l
                 (long long)kMaxM, (long long)N, (long long)M, (long long)leaf_rows);
   if (r_max < 1 || r_max > M) return fail(PYLOM_ERR_SHAPE, "pylom_pod: r_max must be in [1, M]");
   if (ldx < N || ldu < N || ldvt < M) return fail(PYLOM_ERR_ARG, "pylom_pod: leading dimension too small");
-  if (prec != PYLOM_PREC_FP64)
-    return fail(PYLOM_ERR_UNSUPPORTED, "pylom_pod: this build implements PYLOM_PREC_FP64 only");
+  const bool mixed = prec == PYLOM_PREC_MIXED_3XTF32;
   const int64_t P = leaves_of(N, M, leaf_rows);
-  const size_t need = pod_bytes(N, M, P, r_max);
+  const size_t need = pod_bytes(N, M, P, r_max, prec);
   if (!aligned256(ws) || ws_bytes < need)
     return fail(PYLOM_ERR_WORKSPACE, "pylom_pod: workspace needs %zu bytes, 256-byte aligned (got %zu)",
                 need, ws_bytes);
@@ -146,12 +148,13 @@ extern "C" pylom_status pylom_pod(const void* X, int64_t N, int64_t M, int64_t l
   WsHeader* hdr = (WsHeader*)base;
   TsqrState ts;
   ts.hdr = hdr;
-  tsqr_state_carve(ts, base + sizeof(WsHeader), N, M, P, r_max);
-  char* p2 = base + sizeof(WsHeader) + tsqr_state_bytes(N, M, P, r_max);
+  tsqr_state_carve(ts, base + sizeof(WsHeader), N, M, P, r_max, !mixed);
+  char* p2 = base + sizeof(WsHeader) + tsqr_state_bytes(N, M, P, r_max, !mixed);
   SvdState ss;
   ss.hdr = hdr;
   svd_state_carve(ss, p2, M);
   double* UR = (double*)(p2 + svd_state_bytes(M));
+  char* extra = p2 + svd_state_bytes(M) + align256(sizeof(double) * (size_t)M * M);
 
   const bool prof = g_prof.on && g_prof.n < g_prof.cap;
   const int call = g_prof.n;
@@ -160,14 +163,19 @@ extern "C" pylom_status pylom_pod(const void* X, int64_t N, int64_t M, int64_t l
   e = cudaMemsetAsync(ts.arrive, 0, sizeof(unsigned) * (size_t)P, st);
   if (e != cudaSuccess) return cuda_fail(e, "pylom_pod: counter clear");
   if (prof && (e = cudaEventRecord(g_prof.at(call, 0), st)) != cudaSuccess) return cuda_fail(e, "profile");
-  e = launch_tsqr_fp64(ts, X, ldx, xtype, w, remove_mean, mean, st);
+  e = mixed ? launch_tsqr_mixed(ts, extra, X, ldx, xtype, w, remove_mean, mean, st)
+            : launch_tsqr_fp64(ts, X, ldx, xtype, w, remove_mean, mean, st);
   if (e != cudaSuccess) return cuda_fail(e, "pylom_pod: leaf QR / tree");
   if (prof && (e = cudaEventRecord(g_prof.at(call, 1), st)) != cudaSuccess) return cuda_fail(e, "profile");
   e = launch_svd_fp64(ss, ts.Rs, M, UR, M, S, VT, ldvt, 60, energy, r_max, st);
   if (e != cudaSuccess) return cuda_fail(e, "pylom_pod: small SVD");
   if (prof && (e = cudaEventRecord(g_prof.at(call, 2), st)) != cudaSuccess) return cuda_fail(e, "profile");
-  e = launch_modes_fp64(ts, UR, M, -1, w, mode_kind == PYLOM_MODES_PHYSICAL, U, ldu, r_out, st,
-                        prof ? g_prof.at(call, 3) : nullptr);
+  if (mixed)
+    e = launch_modes_mixed(ts, extra, UR, M, -1, w, mode_kind == PYLOM_MODES_PHYSICAL, (float*)U, ldu, r_out, st,
+                           prof ? g_prof.at(call, 3) : nullptr);
+  else
+    e = launch_modes_fp64(ts, UR, M, -1, w, mode_kind == PYLOM_MODES_PHYSICAL, (double*)U, ldu, r_out, st,
+                          prof ? g_prof.at(call, 3) : nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "pylom_pod: modes");
   if (prof) {
     if ((e = cudaEventRecord(g_prof.at(call, 4), st)) != cudaSuccess) return cuda_fail(e, "profile");

@@ -32,8 +32,11 @@ struct SvdState {
   double* V;                // Mp x Mp accumulated rotations
 };
 
-size_t tsqr_state_bytes(int64_t N, int64_t M, int64_t P, int64_t rmax);
-void tsqr_state_carve(TsqrState& s, char* base, int64_t N, int64_t M, int64_t P, int64_t rmax);
+// with_y: include the N x M FP64 working copy (the FP64 path; the mixed
+// path keeps an FP32 copy in its own extra region instead)
+size_t tsqr_state_bytes(int64_t N, int64_t M, int64_t P, int64_t rmax, bool with_y = true);
+void tsqr_state_carve(TsqrState& s, char* base, int64_t N, int64_t M, int64_t P, int64_t rmax,
+                      bool with_y = true);
 size_t svd_state_bytes(int64_t M);
 void svd_state_carve(SvdState& s, char* base, int64_t M);
 
@@ -70,6 +73,19 @@ cudaError_t launch_pod_backward(const TsqrState& fs, const double* UR, const dou
 
 // Records a message for pylom_last_error() on the calling host thread.
 void set_error_message(const char* fmt, ...);
+
+// Top-down pass only (B_root from Ur or the identity, then every tree level).
+cudaError_t launch_down_pass_fp64(const TsqrState& s, const double* Ur, int64_t ldur, int64_t r_fixed,
+                                  cudaStream_t st);
+
+// Mixed-precision leaves (tsqr_mixed.cu): FP32 working copy + 32-column
+// panel factors in an extra region; 3xTF32 block reflectors on tcgen05.
+size_t mixed_extra_bytes(int64_t N, int64_t M, int64_t P);
+cudaError_t launch_tsqr_mixed(const TsqrState& s, char* extra, const void* X, int64_t ldx, int xtype,
+                              const double* w, int remove_mean, double* mean, cudaStream_t st);
+cudaError_t launch_modes_mixed(const TsqrState& s, char* extra, const double* Ur, int64_t ldur, int64_t r_fixed,
+                               const double* w, int physical, float* U, int64_t ldu, int64_t* r_out,
+                               cudaStream_t st, cudaEvent_t mid);
 
 // C = op(A) B in binary64 on the FP64 tensor pipe.
 size_t matmul_ws_bytes(int64_t m, int64_t n, int64_t k);

@@ -164,4 +164,148 @@ __device__ void block_reflector(const VF& V, int nbk, int64_t r0, int64_t r1, do
   }
 }
 
+// Panel factorisation of columns [k, k+nbk) of the stacked pair [Rt; Rb]
+// of two upper-triangular M x M factors (the buffer C of Alg. 1, receiver's
+// R on top).  Reflector c touches only row c of the top and rows 0..c of the
+// bottom: v_c = [e_c; u_c], u_c stored in column c of Rb (rows 0..c), the
+// merged R overwrites Rt.  T (row-major, upper) follows the same forward
+// recurrence as the leaves, with v_p^T v_c = u_p^T u_c (the e parts are
+// disjoint).  Loads bypass L1: the partner's slot was written by another
+// block.  sout needs 2 kNB doubles.
+static __device__ void merge_panel_factor(double* Rt, double* Rb, int64_t M, int64_t k, int nbk,
+                                   double* tau_out, double* sT, double* sred, double* sout) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  double* sd = sout + kNB;   // tau_c * (v_c^T column) of the panel columns
+  double xx;
+  {
+    double v[1] = {0.0};
+    for (int64_t i = tid; i <= k; i += nthr) {
+      const double a = ldcg(Rb + i + k * M);
+      v[0] += a * a;
+    }
+    block_sum<1>(v, sred, sout);
+    xx = sout[0];
+  }
+  for (int jj = 0; jj < nbk; ++jj) {
+    const int64_t c = k + jj;
+    const double alpha = ldcg(Rt + c + c * M);
+    double tau_c = 0.0, beta = alpha, scale = 0.0;
+    if (xx != 0.0) {
+      const double nrm = sqrt(alpha * alpha + xx);
+      beta = (alpha >= 0.0) ? -nrm : nrm;
+      tau_c = (beta - alpha) / beta;
+      scale = 1.0 / (alpha - beta);
+    }
+    // pass A: u_c = scale * bottom column c; dots of u_c with the bottom part
+    // of the later panel columns (q > jj) and with earlier reflectors (q < jj)
+    double acc[kNB];
+#pragma unroll
+    for (int q = 0; q < kNB; ++q) acc[q] = 0.0;
+    for (int64_t i = tid; i <= c; i += nthr) {
+      const double u = ldcg(Rb + i + c * M) * scale;
+      Rb[i + c * M] = u;
+#pragma unroll
+      for (int q = 0; q < kNB; ++q)
+        if (q < nbk && q != jj) acc[q] += u * ldcg(Rb + i + (k + q) * M);
+    }
+    block_sum<kNB>(acc, sred, sout);
+    if (tid == 0) {
+      Rt[c + c * M] = beta;
+      tau_out[jj] = tau_c;
+      for (int p = 0; p < jj; ++p) {
+        double s = 0.0;
+        for (int q = p; q < jj; ++q) s += sT[p * kNB + q] * sout[q];
+        sT[p * kNB + jj] = -tau_c * s;
+      }
+      sT[jj * kNB + jj] = tau_c;
+    }
+    if (tid > jj && tid < nbk) {
+      // the e_c part of v_c contributes the top entry Rt[c, k+q]
+      double* tp = Rt + c + (k + tid) * M;
+      const double d = (sout[tid] + ldcg(tp)) * tau_c;
+      sd[tid] = d;
+      *tp = ldcg(tp) - d;
+    }
+    __syncthreads();
+    // pass B: bottom rows 0..c of the later panel columns; squared norm of
+    // the next column's bottom rows 0..c+1
+    double nx[1] = {0.0};
+    if (jj + 1 < nbk) {
+      for (int64_t i = tid; i <= c + 1; i += nthr) {
+        const double u = (i <= c) ? ldcg(Rb + i + c * M) : 0.0;
+#pragma unroll
+        for (int q = 0; q < kNB; ++q) {
+          if (q > jj && q < nbk) {
+            double* bp = Rb + i + (k + q) * M;
+            double a = ldcg(bp);
+            if (i <= c) {
+              a -= sd[q] * u;
+              *bp = a;
+            }
+            if (q == jj + 1) nx[0] += a * a;
+          }
+        }
+      }
+    }
+    block_sum<1>(nx, sred, sout);
+    xx = sout[0];
+  }
+}
+
+// QR of [Rt; Rb] by panels of kNB columns: structured panel factorisation,
+// then the block reflector applied to the trailing columns on the FP64
+// tensor pipe (bottom rows 0..k+nbk-1 through u, top rows k..k+nbk-1 as the
+// identity block).  Flops (2/3) M^3 as in the paper's cost model.
+static __device__ void tree_merge(double* Rt, double* Rb, double* tau, int64_t M, double* sT, double* sred,
+                           double* sout, double* sW, double* sWp) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int64_t k = 0; k < M; k += kNB) {
+    const int nbk = (int)((M - k) < kNB ? (M - k) : kNB);
+    for (int idx = tid; idx < kSmT; idx += nthr) sT[idx] = 0.0;
+    __syncthreads();
+    merge_panel_factor(Rt, Rb, M, k, nbk, tau + k, sT, sred, sout);
+    __syncthreads();
+    if (k + nbk < M) {
+      MergeV V{Rb, M, k, nbk};
+      block_reflector<true, true>(V, nbk, 0, k + nbk, Rb + (k + nbk) * M, M, (int)(M - k - nbk),
+                                  Rt + k + (k + nbk) * M, M, sT, sW, sWp);
+    }
+    __syncthreads();
+  }
+}
+
+// Binary tree of Alg. 1 run by the block that finished leaf `leaf`: at step
+// 2^l the subtree rooted at `node` pairs with node ^ 2^l; a missing partner
+// (>= P) passes R up unchanged; the first block to arrive at a merge leaves,
+// the second merges (left child's R on top, as the receiver keeps its R in
+// the upper half of C in Alg. 1).  Shared-memory buffers as the leaf's.
+static __device__ void tree_climb(const TsqrState& s, int64_t leaf, double* sT, double* sred, double* sout,
+                                  double* sW, double* sWp) {
+  __shared__ unsigned s_prev;
+  const int tid = threadIdx.x;
+  const int64_t M = s.M;
+  int64_t node = leaf;
+  for (int64_t step = 1; step < s.P; step <<= 1) {
+    int64_t left, right;
+    if (node & step) {
+      left = node - step;
+      right = node;
+    } else {
+      right = node + step;
+      if (right >= s.P) continue;
+      left = node;
+    }
+    if (tid == 0) s_prev = atomicAdd(&s.arrive[right], 1u);
+    __syncthreads();
+    const unsigned prev = s_prev;
+    __syncthreads();
+    if (prev == 0) return;  // first to arrive: the partner merges
+    __threadfence();
+    tree_merge(s.Rs + left * M * M, s.Rs + right * M * M, s.tau_tree + right * M, M, sT, sred, sout, sW, sWp);
+    __threadfence();
+    __syncthreads();
+    node = left;
+  }
+}
+
 }  // namespace pylom

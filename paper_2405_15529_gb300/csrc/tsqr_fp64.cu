@@ -92,116 +92,6 @@ __device__ void panel_factor(double* A, int64_t lda, int64_t k, int nbk, int64_t
   }
 }
 
-// Panel factorisation of columns [k, k+nbk) of the stacked pair [Rt; Rb]
-// of two upper-triangular M x M factors (the buffer C of Alg. 1, receiver's
-// R on top).  Reflector c touches only row c of the top and rows 0..c of the
-// bottom: v_c = [e_c; u_c], u_c stored in column c of Rb (rows 0..c), the
-// merged R overwrites Rt.  T (row-major, upper) follows the same forward
-// recurrence as the leaves, with v_p^T v_c = u_p^T u_c (the e parts are
-// disjoint).  Loads bypass L1: the partner's slot was written by another
-// block.  sout needs 2 kNB doubles.
-__device__ void merge_panel_factor(double* Rt, double* Rb, int64_t M, int64_t k, int nbk,
-                                   double* tau_out, double* sT, double* sred, double* sout) {
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  double* sd = sout + kNB;   // tau_c * (v_c^T column) of the panel columns
-  double xx;
-  {
-    double v[1] = {0.0};
-    for (int64_t i = tid; i <= k; i += nthr) {
-      const double a = ldcg(Rb + i + k * M);
-      v[0] += a * a;
-    }
-    block_sum<1>(v, sred, sout);
-    xx = sout[0];
-  }
-  for (int jj = 0; jj < nbk; ++jj) {
-    const int64_t c = k + jj;
-    const double alpha = ldcg(Rt + c + c * M);
-    double tau_c = 0.0, beta = alpha, scale = 0.0;
-    if (xx != 0.0) {
-      const double nrm = sqrt(alpha * alpha + xx);
-      beta = (alpha >= 0.0) ? -nrm : nrm;
-      tau_c = (beta - alpha) / beta;
-      scale = 1.0 / (alpha - beta);
-    }
-    // pass A: u_c = scale * bottom column c; dots of u_c with the bottom part
-    // of the later panel columns (q > jj) and with earlier reflectors (q < jj)
-    double acc[kNB];
-#pragma unroll
-    for (int q = 0; q < kNB; ++q) acc[q] = 0.0;
-    for (int64_t i = tid; i <= c; i += nthr) {
-      const double u = ldcg(Rb + i + c * M) * scale;
-      Rb[i + c * M] = u;
-#pragma unroll
-      for (int q = 0; q < kNB; ++q)
-        if (q < nbk && q != jj) acc[q] += u * ldcg(Rb + i + (k + q) * M);
-    }
-    block_sum<kNB>(acc, sred, sout);
-    if (tid == 0) {
-      Rt[c + c * M] = beta;
-      tau_out[jj] = tau_c;
-      for (int p = 0; p < jj; ++p) {
-        double s = 0.0;
-        for (int q = p; q < jj; ++q) s += sT[p * kNB + q] * sout[q];
-        sT[p * kNB + jj] = -tau_c * s;
-      }
-      sT[jj * kNB + jj] = tau_c;
-    }
-    if (tid > jj && tid < nbk) {
-      // the e_c part of v_c contributes the top entry Rt[c, k+q]
-      double* tp = Rt + c + (k + tid) * M;
-      const double d = (sout[tid] + ldcg(tp)) * tau_c;
-      sd[tid] = d;
-      *tp = ldcg(tp) - d;
-    }
-    __syncthreads();
-    // pass B: bottom rows 0..c of the later panel columns; squared norm of
-    // the next column's bottom rows 0..c+1
-    double nx[1] = {0.0};
-    if (jj + 1 < nbk) {
-      for (int64_t i = tid; i <= c + 1; i += nthr) {
-        const double u = (i <= c) ? ldcg(Rb + i + c * M) : 0.0;
-#pragma unroll
-        for (int q = 0; q < kNB; ++q) {
-          if (q > jj && q < nbk) {
-            double* bp = Rb + i + (k + q) * M;
-            double a = ldcg(bp);
-            if (i <= c) {
-              a -= sd[q] * u;
-              *bp = a;
-            }
-            if (q == jj + 1) nx[0] += a * a;
-          }
-        }
-      }
-    }
-    block_sum<1>(nx, sred, sout);
-    xx = sout[0];
-  }
-}
-
-// QR of [Rt; Rb] by panels of kNB columns: structured panel factorisation,
-// then the block reflector applied to the trailing columns on the FP64
-// tensor pipe (bottom rows 0..k+nbk-1 through u, top rows k..k+nbk-1 as the
-// identity block).  Flops (2/3) M^3 as in the paper's cost model.
-__device__ void tree_merge(double* Rt, double* Rb, double* tau, int64_t M, double* sT, double* sred,
-                           double* sout, double* sW, double* sWp) {
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  for (int64_t k = 0; k < M; k += kNB) {
-    const int nbk = (int)((M - k) < kNB ? (M - k) : kNB);
-    for (int idx = tid; idx < kSmT; idx += nthr) sT[idx] = 0.0;
-    __syncthreads();
-    merge_panel_factor(Rt, Rb, M, k, nbk, tau + k, sT, sred, sout);
-    __syncthreads();
-    if (k + nbk < M) {
-      MergeV V{Rb, M, k, nbk};
-      block_reflector<true, true>(V, nbk, 0, k + nbk, Rb + (k + nbk) * M, M, (int)(M - k - nbk),
-                                  Rt + k + (k + nbk) * M, M, sT, sW, sWp);
-    }
-    __syncthreads();
-  }
-}
-
 struct LeafArgs {
   TsqrState s;
   const void* X;
@@ -287,30 +177,7 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_qr_kernel(LeafArgs a) {
   __threadfence();
   __syncthreads();
 
-  // Binary tree of Alg. 1: at step 2^l the subtree rooted at `node` pairs
-  // with node ^ 2^l; a missing partner (>= P) passes R up unchanged.
-  __shared__ unsigned s_prev;
-  int64_t node = leaf;
-  for (int64_t step = 1; step < s.P; step <<= 1) {
-    int64_t left, right;
-    if (node & step) {
-      left = node - step;
-      right = node;
-    } else {
-      right = node + step;
-      if (right >= s.P) continue;
-      left = node;
-    }
-    if (tid == 0) s_prev = atomicAdd(&s.arrive[right], 1u);
-    __syncthreads();
-    if (s_prev == 0) return;  // first to arrive: the partner merges
-    __threadfence();
-    tree_merge(s.Rs + left * M * M, s.Rs + right * M * M, s.tau_tree + right * M, M, sT, sred,
-               sout, sW, sWp);
-    __threadfence();
-    __syncthreads();
-    node = left;
-  }
+  tree_climb(s, leaf, sT, sred, sout, sW, sWp);
 }
 
 // Top-down pass (the broadcast loop of Alg. 1): at a merge of `left` and
@@ -408,10 +275,10 @@ __global__ void copy_root_kernel(TsqrState s, double* R, int64_t ldr) {
 // host side
 // ---------------------------------------------------------------------------
 
-size_t tsqr_state_bytes(int64_t N, int64_t M, int64_t P, int64_t rmax) {
+size_t tsqr_state_bytes(int64_t N, int64_t M, int64_t P, int64_t rmax, bool with_y) {
   const int64_t npan = (M + kNB - 1) / kNB;
   size_t b = 0;
-  b += align256(sizeof(double) * (size_t)N * M);
+  if (with_y) b += align256(sizeof(double) * (size_t)N * M);
   b += align256(sizeof(double) * (size_t)P * M);
   b += align256(sizeof(double) * (size_t)P * npan * kNB * kNB);
   b += align256(sizeof(double) * (size_t)P * M * M);
@@ -421,14 +288,15 @@ size_t tsqr_state_bytes(int64_t N, int64_t M, int64_t P, int64_t rmax) {
   return b;
 }
 
-void tsqr_state_carve(TsqrState& s, char* base, int64_t N, int64_t M, int64_t P, int64_t rmax) {
+void tsqr_state_carve(TsqrState& s, char* base, int64_t N, int64_t M, int64_t P, int64_t rmax, bool with_y) {
   s.N = N;
   s.M = M;
   s.P = P;
   s.npan = (M + kNB - 1) / kNB;
   s.rmax = rmax;
   char* p = base;
-  s.Y = (double*)p;        p += align256(sizeof(double) * (size_t)N * M);
+  s.Y = with_y ? (double*)p : nullptr;
+  if (with_y) p += align256(sizeof(double) * (size_t)N * M);
   s.tau = (double*)p;      p += align256(sizeof(double) * (size_t)P * M);
   s.T = (double*)p;        p += align256(sizeof(double) * (size_t)P * s.npan * kNB * kNB);
   s.Rs = (double*)p;       p += align256(sizeof(double) * (size_t)P * M * M);
@@ -460,9 +328,8 @@ cudaError_t launch_copy_root_r(const TsqrState& s, double* R, int64_t ldr, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_modes_fp64(const TsqrState& s, const double* Ur, int64_t ldur, int64_t r_fixed,
-                              const double* w, int physical, double* U, int64_t ldu,
-                              int64_t* r_out, cudaStream_t st, cudaEvent_t mid) {
+cudaError_t launch_down_pass_fp64(const TsqrState& s, const double* Ur, int64_t ldur, int64_t r_fixed,
+                                  cudaStream_t st) {
   init_root_kernel<<<64, 256, 0, st>>>(s, Ur, ldur, r_fixed);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -476,6 +343,14 @@ cudaError_t launch_modes_fp64(const TsqrState& s, const double* Ur, int64_t ldur
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  return cudaSuccess;
+}
+
+cudaError_t launch_modes_fp64(const TsqrState& s, const double* Ur, int64_t ldur, int64_t r_fixed,
+                              const double* w, int physical, double* U, int64_t ldu,
+                              int64_t* r_out, cudaStream_t st, cudaEvent_t mid) {
+  cudaError_t e = launch_down_pass_fp64(s, Ur, ldur, r_fixed, st);
+  if (e != cudaSuccess) return e;
   if (mid) {
     e = cudaEventRecord(mid, st);
     if (e != cudaSuccess) return e;

@@ -114,10 +114,10 @@ def test_pod_reports_nonfinite_input():
     assert ei.value.status == pg.ERR_NONFINITE
 
 
-def test_pod_rejects_mixed_until_built():
+def test_tsqr_is_fp64_only():
     X = _dev(synth.waves(1000, 10, n_waves=2, noise=0.0))
     with pytest.raises(pg.PylomError):
-        pg.pod(X, prec=pg.PREC_MIXED_3XTF32)
+        pg.tsqr(X, prec=pg.PREC_MIXED_3XTF32)
 
 
 # ---------------------------------------------------------------------------
