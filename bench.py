@@ -153,6 +153,64 @@ def bench_adjoint(args, dev):
     return out
 
 
+def bench_mixed(args, dev):
+    """The 4,194,304 x 256 float32 known-spectrum matrix through the mixed
+    path (FP32 leaves, 3xTF32 block reflectors on tcgen05, FP64 tree and
+    SVD) and, once, through the FP64 path on the same X."""
+    import numpy as np
+    import torch
+    import paper_2405_15529_gb300 as pg
+    import synth
+    N, M = args.rows, M_FULL
+    XT, w, s = synth.known_spectrum_torch(N, M, device=dev, dtype=torch.float32)
+    X = XT.t()
+    prec = pg.PREC_MIXED_3XTF32
+    ws = torch.empty(pg.pod_workspace_size(N, M, 0, M, pg.F32, prec), dtype=torch.uint8, device=dev)
+    U = pg.empty_colmajor(N, M, torch.float32, dev)
+    S = torch.empty(M, dtype=torch.float64, device=dev)
+    VT = pg.empty_colmajor(M, M, torch.float64, dev)
+    r_dev = torch.zeros(1, dtype=torch.int64, device=dev)
+    out = (U, S, VT, None, r_dev)
+
+    def step():
+        pg.pod(X, w=w, remove_mean=False, energy=ENERGY, r_max=M, prec=prec, workspace=ws, out=out, check=False)
+
+    for _ in range(args.warmup):
+        step()
+    st, r, sweeps = pg.workspace_status(ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pg.profile_begin(args.steps)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    phases, n = pg.profile_end()
+    ms = e0.elapsed_time(e1) / args.steps
+    S_mix = S.cpu().numpy()
+    ref = pg.pod(X, w=w, remove_mean=False, energy=ENERGY)
+    t0 = torch.cuda.Event(enable_timing=True); t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    ref = pg.pod(X, w=w, remove_mean=False, energy=ENERGY)
+    t1.record()
+    torch.cuda.synchronize()
+    ms64 = t0.elapsed_time(t1)
+    S64 = ref.S.cpu().numpy()
+    leaf_ms = phases["leaf_qr_tree"] / max(n, 1)
+    out = {"workload": f"known_spectrum_{N}x{M}_f32_weighted_energy0.99", "status": st, "r": r,
+           "ms_per_step": ms, "value": N * M * 4 / (ms * 1e-3) / 1e9, "unit": "GB/s of X (float32)",
+           "phases_ms_per_step": {k: v / max(n, 1) for k, v in phases.items()},
+           "fp64_path_ms_same_x": ms64, "speedup_vs_fp64_path": ms64 / ms,
+           "sigma_max_abs_diff_vs_fp64_path_over_smax": float(np.max(np.abs(S_mix - S64)) / S64[0]),
+           "sigma_max_abs_err_vs_closed_form_over_smax": float(np.max(np.abs(S_mix - s)) / s[0]),
+           "leaf_kernel": {"kernel": "leaf_qr_mixed_kernel (FP32 panels + 3xTF32 tcgen05 trailing updates + FP64 tree)",
+                           "ms_per_launch": leaf_ms,
+                           "useful_tflops": 2.0 * N * M * M / (leaf_ms * 1e-3) / 1e12}}
+    del X, XT, w, ws, U, S, VT, r_dev, ref
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_spod(args, dev):
     """All 256 SPOD bins (complex64, N_f log-uniform in [2^16, 2^20], Nb_f in
     [16, 128]) in one persistent launch captured in a CUDA graph."""
@@ -366,6 +424,8 @@ def run_ours(args, rank, world, local_rank):
     del XT, X, ws, U, S, VT, r_dev, out
     torch.cuda.empty_cache()
     extra = {}
+    if world == 1 and not args.no_mixed:
+        extra["mixed_3xtf32"] = bench_mixed(args, dev)
     if world == 1 and not args.no_adjoint:
         extra["adjoint"] = bench_adjoint(args, dev)
     if world == 1 and not args.no_spod:
@@ -414,6 +474,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-spod", action="store_true")
     ap.add_argument("--adj-steps", type=int, default=3)
     ap.add_argument("--spod-steps", type=int, default=3)

@@ -55,6 +55,7 @@ struct MixedArgs {
   TsqrState s;
   float* Yf;          // N x M fp32 working copy (ld N) -> reflectors
   double* T2;         // per leaf and panel: kNB2 x kNB2 (row-major) fp64
+  float* Pb;          // N x kNB2 row-major panel buffers (leaf rows)
   const void* X;
   int64_t ldx;
   int xtype;
@@ -92,14 +93,32 @@ __device__ __forceinline__ void block_sum_d(double (&v)[K], double* scratch, dou
 // two-pass-per-column scheme as the FP64 leaves: scale v_j and form its dot
 // products with the panel, then update the panel and the next norm.  Sums
 // are compensated FP32 per thread and FP64 across threads.
+// The passes run on a row-major copy of the panel (Pb: leaf rows k..h-1, 32
+// contiguous floats = 128 bytes per row), so every pass streams contiguous
+// rows instead of 32 columns that are N elements apart; the panel is
+// gathered before and scattered back to the column-major leaf after.
 __device__ void panel_factor_mixed(float* Y, int64_t ldy, int64_t k, int nbk, int64_t h, double* tau_out,
-                                   double* sT, double* sred, double* sout) {
+                                   double* sT, double* sred, double* sout, float* Pb) {
   const int tid = threadIdx.x, nthr = blockDim.x;
+  // gather: Pb[(i - k) * 32 + c] = Y[i, k + c] (zeros beyond nbk)
+  for (int64_t i = k + tid; i < h; i += nthr) {
+    float4* pr = (float4*)(Pb + (i - k) * kNB2);
+#pragma unroll
+    for (int q = 0; q < kNB2 / 4; ++q) {
+      float4 v;
+      v.x = (4 * q + 0 < nbk) ? Y[i + (k + 4 * q + 0) * ldy] : 0.f;
+      v.y = (4 * q + 1 < nbk) ? Y[i + (k + 4 * q + 1) * ldy] : 0.f;
+      v.z = (4 * q + 2 < nbk) ? Y[i + (k + 4 * q + 2) * ldy] : 0.f;
+      v.w = (4 * q + 3 < nbk) ? Y[i + (k + 4 * q + 3) * ldy] : 0.f;
+      pr[q] = v;
+    }
+  }
+  __syncthreads();
   double xx;
   {
     KSum32 ks;
     for (int64_t i = k + 1 + tid; i < h; i += nthr) {
-      const float a = Y[i + k * ldy];
+      const float a = Pb[(i - k) * kNB2];
       ks.add(a * a);
     }
     double v[1] = {ks.get()};
@@ -108,7 +127,7 @@ __device__ void panel_factor_mixed(float* Y, int64_t ldy, int64_t k, int nbk, in
   }
   for (int jj = 0; jj < nbk; ++jj) {
     const int64_t j = k + jj;
-    const double alpha = (double)Y[j + j * ldy];
+    const double alpha = (double)Pb[(j - k) * kNB2 + jj];
     double tau_j = 0.0, beta = alpha, scale = 0.0;
     if (xx != 0.0) {
       const double nrm = sqrt(alpha * alpha + xx);
@@ -119,21 +138,32 @@ __device__ void panel_factor_mixed(float* Y, int64_t ldy, int64_t k, int nbk, in
     const float scf = (float)scale;
     KSum32 acc[kNB2];
     for (int64_t i = j + tid; i < h; i += nthr) {
+      float row[kNB2];
+      const float4* pr = (const float4*)(Pb + (i - k) * kNB2);
+#pragma unroll
+      for (int q = 0; q < kNB2 / 4; ++q) {
+        const float4 v4 = pr[q];
+        row[4 * q] = v4.x; row[4 * q + 1] = v4.y; row[4 * q + 2] = v4.z; row[4 * q + 3] = v4.w;
+      }
+      float rj = 0.f;   // row[jj] without a runtime index (keeps row[] in registers)
+#pragma unroll
+      for (int c = 0; c < kNB2; ++c)
+        if (c == jj) rj = row[c];
       float v = 1.f;
       if (i != j) {
-        v = Y[i + j * ldy] * scf;
-        Y[i + j * ldy] = v;
+        v = rj * scf;
+        Pb[(i - k) * kNB2 + jj] = v;
       }
 #pragma unroll
       for (int c = 0; c < kNB2; ++c)
-        if (c < nbk && c != jj) acc[c].add(v * Y[i + (k + c) * ldy]);
+        if (c < nbk && c != jj) acc[c].add(v * row[c]);
     }
     double dv[kNB2];
 #pragma unroll
     for (int c = 0; c < kNB2; ++c) dv[c] = acc[c].get();
     block_sum_d<kNB2>(dv, sred, sout);
     if (tid == 0) {
-      Y[j + j * ldy] = (float)beta;
+      Pb[(j - k) * kNB2 + jj] = (float)beta;
       tau_out[jj] = tau_j;
       for (int p = 0; p < jj; ++p) {
         double s = 0.0;
@@ -142,24 +172,54 @@ __device__ void panel_factor_mixed(float* Y, int64_t ldy, int64_t k, int nbk, in
       }
       sT[jj * kNB2 + jj] = tau_j;
     }
+    float fc[kNB2];
+#pragma unroll
+    for (int c = 0; c < kNB2; ++c) fc[c] = (c > jj && c < nbk) ? (float)(tau_j * sout[c]) : 0.f;
     KSum32 nx;
     if (jj + 1 < nbk) {
       for (int64_t i = j + tid; i < h; i += nthr) {
-        const float v = (i == j) ? 1.f : Y[i + j * ldy];
+        float4* pr = (float4*)(Pb + (i - k) * kNB2);
+        float row[kNB2];
+#pragma unroll
+        for (int q = 0; q < kNB2 / 4; ++q) {
+          const float4 v4 = pr[q];
+          row[4 * q] = v4.x; row[4 * q + 1] = v4.y; row[4 * q + 2] = v4.z; row[4 * q + 3] = v4.w;
+        }
+        float rj = 0.f;
+#pragma unroll
+        for (int c = 0; c < kNB2; ++c)
+          if (c == jj) rj = row[c];
+        const float v = (i == j) ? 1.f : rj;
+        float rn = 0.f;
 #pragma unroll
         for (int c = 0; c < kNB2; ++c) {
-          if (c > jj && c < nbk) {
-            const float a = Y[i + (k + c) * ldy] - (float)(tau_j * sout[c]) * v;
-            Y[i + (k + c) * ldy] = a;
-            if (c == jj + 1 && i > j + 1) nx.add(a * a);
-          }
+          if (c > jj) row[c] -= fc[c] * v;
+          if (c == jj + 1) rn = row[c];
         }
+        if (i > j + 1) nx.add(rn * rn);
+        // write back the updated columns (the leading ones are unchanged)
+#pragma unroll
+        for (int q = 0; q < kNB2 / 4; ++q)
+          if (4 * q + 3 > jj) pr[q] = make_float4(row[4 * q], row[4 * q + 1], row[4 * q + 2], row[4 * q + 3]);
       }
     }
     double nv[1] = {nx.get()};
     block_sum_d<1>(nv, sred, sout);
     xx = sout[0];
   }
+  // scatter the factored panel (R above the diagonal, reflectors below) back
+  for (int64_t i = k + tid; i < h; i += nthr) {
+    const float4* pr = (const float4*)(Pb + (i - k) * kNB2);
+#pragma unroll
+    for (int q = 0; q < kNB2 / 4; ++q) {
+      const float4 v = pr[q];
+      if (4 * q + 0 < nbk) Y[i + (k + 4 * q + 0) * ldy] = v.x;
+      if (4 * q + 1 < nbk) Y[i + (k + 4 * q + 1) * ldy] = v.y;
+      if (4 * q + 2 < nbk) Y[i + (k + 4 * q + 2) * ldy] = v.z;
+      if (4 * q + 3 < nbk) Y[i + (k + 4 * q + 3) * ldy] = v.w;
+    }
+  }
+  __syncthreads();
 }
 
 // Issue the K-slices of a 3xTF32 product from the four shared tiles (rows
@@ -202,24 +262,39 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
     const int64_t nkc = (L + kKC - 1) / kKC;
     for (int64_t kc = 0; kc < nkc && ok; ++kc) {
       const int64_t rb = k + kc * kKC;
-      // A = C^T chunk: row = column c (0..127), K = row i (0..31); warp w takes columns c = w, w+4, ...
-      for (int c = warp; c < kCH; c += 4) {
+      // A = C^T chunk: row = column c (0..127), K = row i (0..31); warp w
+      // takes columns c = w + 4u, lane = row; 8 loads in flight per batch
+      {
         const int64_t row = rb + lane;
-        const float x = (c < wc && row < h) ? C[row + (int64_t)(c0 + c) * ldc] : 0.f;
-        float hi, lo;
-        split_tf32(x, hi, lo);
-        const uint32_t o = cm_off(c, lane, kKC);
-        *(float*)(smem + kOffA + o) = hi;
-        *(float*)(smem + kOffAlo + o) = lo;
-      }
-      // B = V chunk: row = reflector p (0..31), K = row i
-      for (int p = warp; p < kNB2; p += 4) {
-        const float x = vval_f(Y, ldy, k, nbk, h, rb + lane, p);
-        float hi, lo;
-        split_tf32(x, hi, lo);
-        const uint32_t o = cm_off(p, lane, kKC);
-        *(float*)(smem + kOffB + o) = hi;
-        *(float*)(smem + kOffBlo + o) = lo;
+        const bool rok = row < h;
+        for (int cb = 0; cb < kCH; cb += 32) {
+          float x[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int c = cb + warp + 4 * u;
+            x[u] = (rok && c < wc) ? C[row + (int64_t)(c0 + c) * ldc] : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            float hi, lo;
+            split_tf32(x[u], hi, lo);
+            const uint32_t o = cm_off(cb + warp + 4 * u, lane, kKC);
+            *(float*)(smem + kOffA + o) = hi;
+            *(float*)(smem + kOffAlo + o) = lo;
+          }
+        }
+        // B = V chunk: row = reflector p (0..31), K = row i
+        float x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = vval_f(Y, ldy, k, nbk, h, rb + lane, warp + 4 * u);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          float hi, lo;
+          split_tf32(x[u], hi, lo);
+          const uint32_t o = cm_off(warp + 4 * u, lane, kKC);
+          *(float*)(smem + kOffB + o) = hi;
+          *(float*)(smem + kOffBlo + o) = lo;
+        }
       }
       fence_smem_async();
       fence_before();
@@ -276,13 +351,17 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
     const int64_t nrt = (L + kRT - 1) / kRT;
     for (int64_t rt = 0; rt < nrt && ok; ++rt) {
       const int64_t rb = k + rt * kRT;
-      // A = V rows: row = r (0..127), K = p (0..31); thread t takes row t
+      // A = V rows: row = r (0..127), K = p (0..31); thread t takes row t,
+      // all 32 loads issued before use
       {
         const int r = tid;
+        float x[kNB2];
+#pragma unroll
+        for (int p = 0; p < kNB2; ++p) x[p] = vval_f(Y, ldy, k, nbk, h, rb + r, p);
+#pragma unroll
         for (int p = 0; p < kNB2; ++p) {
-          const float x = vval_f(Y, ldy, k, nbk, h, rb + r, p);
           float hi, lo;
-          split_tf32(x, hi, lo);
+          split_tf32(x[p], hi, lo);
           const uint32_t o = cm_off(r, p, kNB2);
           *(float*)(smem + kOffA + o) = hi;
           *(float*)(smem + kOffAlo + o) = lo;
@@ -307,13 +386,13 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
         tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, v);
         tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(kCH + cc), vx);
         if (row < h) {
+          float cv[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            if (cc + j < wc) {
-              float* cp = C + row + (int64_t)(c0 + cc + j) * ldc;
-              *cp = *cp + (v[j] + vx[j]);
-            }
-          }
+          for (int j = 0; j < 16; ++j)
+            cv[j] = (cc + j < wc) ? C[row + (int64_t)(c0 + cc + j) * ldc] : 0.f;
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (cc + j < wc) C[row + (int64_t)(c0 + cc + j) * ldc] = cv[j] + (v[j] + vx[j]);
         }
       }
       fence_before();
@@ -383,7 +462,7 @@ __global__ void __launch_bounds__(kMxThreads) leaf_qr_mixed_kernel(MixedArgs a) 
     const int nbk = (int)((M - k) < kNB2 ? (M - k) : kNB2);
     for (int idx = tid; idx < kNB2 * kNB2; idx += blockDim.x) sT[idx] = 0.0;
     __syncthreads();
-    panel_factor_mixed(Y, ldy, k, nbk, h, s.tau + leaf * M + k, sT, sred, sout);
+    panel_factor_mixed(Y, ldy, k, nbk, h, s.tau + leaf * M + k, sT, sred, sout, a.Pb + r0 * kNB2);
     __syncthreads();
     double* Tg = a.T2 + (leaf * npan + k / kNB2) * kNB2 * kNB2;
     for (int idx = tid; idx < kNB2 * kNB2; idx += blockDim.x) Tg[idx] = sT[idx];
@@ -475,7 +554,8 @@ __global__ void __launch_bounds__(kMxThreads) modes_mixed_kernel(TsqrState s, co
 
 size_t mixed_extra_bytes(int64_t N, int64_t M, int64_t P) {
   const int64_t npan = (M + kNB2 - 1) / kNB2;
-  return align256(sizeof(float) * (size_t)N * M) + align256(sizeof(double) * (size_t)P * npan * kNB2 * kNB2);
+  return align256(sizeof(float) * (size_t)N * M) + align256(sizeof(double) * (size_t)P * npan * kNB2 * kNB2) +
+         align256(sizeof(float) * (size_t)N * kNB2);
 }
 
 cudaError_t launch_tsqr_mixed(const TsqrState& s, char* extra, const void* X, int64_t ldx, int xtype,
@@ -489,8 +569,10 @@ cudaError_t launch_tsqr_mixed(const TsqrState& s, char* extra, const void* X, in
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  MixedArgs a{s, (float*)extra, (double*)(extra + align256(sizeof(float) * (size_t)s.N * s.M)), X, ldx, xtype, w,
-              remove_mean, mean};
+  const int64_t npan = (s.M + kNB2 - 1) / kNB2;
+  char* t2 = extra + align256(sizeof(float) * (size_t)s.N * s.M);
+  char* pb = t2 + align256(sizeof(double) * (size_t)s.P * npan * kNB2 * kNB2);
+  MixedArgs a{s, (float*)extra, (double*)t2, (float*)pb, X, ldx, xtype, w, remove_mean, mean};
   leaf_qr_mixed_kernel<<<(unsigned)s.P, kMxThreads, kMixSmemTotal, st>>>(a);
   return cudaGetLastError();
 }
