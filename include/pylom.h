@@ -84,6 +84,15 @@ const char* pylom_last_error(void);
  * Returns -1 on invalid arguments. */
 int64_t pylom_leaf_count(int64_t N, int64_t M, int64_t leaf_rows);
 
+/* Tree reduction of the leaf R factors (Sec. 3.1, the reduce loop of
+ * Alg. 1), used by pylom_pod and pylom_tsqr.  Below 384 columns the leaf
+ * kernels merge pairs as they finish (the second block to reach a merge
+ * performs it); from 384 columns on, one cooperative launch after the
+ * leaves spreads every merge of a level over all thread blocks, one panel
+ * of 16 columns per grid-wide step.  Both leave the same pairing, merged R
+ * and node reflectors.  The environment variable PYLOM_TREE = "climb" or
+ * "coop", read at each call, forces one form (testing and tuning). */
+
 /* Device status recorded in a workspace by the last call that used it.
  * Synchronises `stream`, then returns the recorded pylom_status
  * (PYLOM_OK if none) and, when the pointers are non-NULL, writes to HOST

@@ -9,6 +9,9 @@ namespace pylom {
 
 // Householder panel width of the FP64 leaf QR (two 8-row DMMA tiles).
 constexpr int kNB = 16;
+// From this many columns on, the tree merges run in tree_coop_kernel.
+constexpr int64_t kCoopTreeMinM = 384;
+bool use_climb_tree(int64_t M, int64_t P);
 
 // Device pointers of one TSQR (+ modes) problem, carved from a workspace.
 struct TsqrState {
@@ -23,6 +26,8 @@ struct TsqrState {
   unsigned* arrive;         // P arrival counters of the tree merges
   double* B;                // P x M x rmax down-pass blocks (nullable if no modes)
   int64_t rmax;
+  double* Tt;               // 2 x ceil(P/2) x kNB x kNB: panel T factors of the cooperative tree
+  int climb;                // 1: leaves run the last-arriver tree; 0: tree_coop_kernel follows them
 };
 
 struct SvdState {
@@ -44,6 +49,10 @@ void svd_state_carve(SvdState& s, char* base, int64_t M);
 // last-arriver tree reduction; the root R ends in Rs[0].
 cudaError_t launch_tsqr_fp64(const TsqrState& s, const void* X, int64_t ldx, int xtype,
                              const double* w, int remove_mean, double* mean, cudaStream_t st);
+
+// The tree reduction as one cooperative launch over all blocks (for large
+// M); runs after the leaf kernel when s.climb == 0.
+cudaError_t launch_tree_coop(const TsqrState& s, cudaStream_t st);
 
 // Copy the root R (upper triangle) into an M x M matrix with zeros below.
 cudaError_t launch_copy_root_r(const TsqrState& s, double* R, int64_t ldr, cudaStream_t st);

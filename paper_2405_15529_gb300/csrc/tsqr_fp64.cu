@@ -15,6 +15,9 @@
 // thread blocks: at every level the block that finishes second merges the
 // pair (left child's R on top, as the receiver keeps its own R in the upper
 // half of C in Alg. 1), so no block ever waits on another.
+#include <stdlib.h>
+#include <string.h>
+
 #include "kernels.h"
 #include "reflectors.cuh"
 
@@ -177,7 +180,7 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_qr_kernel(LeafArgs a) {
   __threadfence();
   __syncthreads();
 
-  tree_climb(s, leaf, sT, sred, sout, sW, sWp);
+  if (s.climb) tree_climb(s, leaf, sT, sred, sout, sW, sWp);
 }
 
 // Top-down pass (the broadcast loop of Alg. 1): at a merge of `left` and
@@ -275,6 +278,17 @@ __global__ void copy_root_kernel(TsqrState s, double* R, int64_t ldr) {
 // host side
 // ---------------------------------------------------------------------------
 
+// Which tree: the last-arriver climb inside the leaf kernel overlaps the
+// merges with leaves still running and wins while a merge is cheap; from
+// kCoopTreeMinM columns on, a merge is spread over all blocks instead.  The
+// environment variable PYLOM_TREE ("climb" or "coop") overrides the choice.
+bool use_climb_tree(int64_t M, int64_t P) {
+  const char* env = getenv("PYLOM_TREE");
+  if (env && strcmp(env, "climb") == 0) return true;
+  if (env && strcmp(env, "coop") == 0) return false;
+  return M < kCoopTreeMinM || P <= 1;
+}
+
 size_t tsqr_state_bytes(int64_t N, int64_t M, int64_t P, int64_t rmax, bool with_y) {
   const int64_t npan = (M + kNB - 1) / kNB;
   size_t b = 0;
@@ -284,6 +298,7 @@ size_t tsqr_state_bytes(int64_t N, int64_t M, int64_t P, int64_t rmax, bool with
   b += align256(sizeof(double) * (size_t)P * M * M);
   b += align256(sizeof(double) * (size_t)P * M);
   b += align256(sizeof(unsigned) * (size_t)P);
+  b += align256(sizeof(double) * (size_t)2 * ((P + 1) / 2) * kSmT);
   b += align256(sizeof(double) * (size_t)P * M * rmax);
   return b;
 }
@@ -302,7 +317,9 @@ void tsqr_state_carve(TsqrState& s, char* base, int64_t N, int64_t M, int64_t P,
   s.Rs = (double*)p;       p += align256(sizeof(double) * (size_t)P * M * M);
   s.tau_tree = (double*)p; p += align256(sizeof(double) * (size_t)P * M);
   s.arrive = (unsigned*)p; p += align256(sizeof(unsigned) * (size_t)P);
+  s.Tt = (double*)p;       p += align256(sizeof(double) * (size_t)2 * ((P + 1) / 2) * kSmT);
   s.B = rmax > 0 ? (double*)p : nullptr;
+  s.climb = use_climb_tree(M, P) ? 1 : 0;
 }
 
 cudaError_t launch_tsqr_fp64(const TsqrState& s, const void* X, int64_t ldx, int xtype,
@@ -320,7 +337,9 @@ cudaError_t launch_tsqr_fp64(const TsqrState& s, const void* X, int64_t ldx, int
   }
   LeafArgs a{s, X, ldx, xtype, w, remove_mean, mean};
   leaf_qr_kernel<<<(unsigned)s.P, kLeafThreads, kLeafSmemBytes, st>>>(a);
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess || s.climb) return e;
+  return launch_tree_coop(s, st);
 }
 
 cudaError_t launch_copy_root_r(const TsqrState& s, double* R, int64_t ldr, cudaStream_t st) {

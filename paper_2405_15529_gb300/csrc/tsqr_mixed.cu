@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(kMxThreads) leaf_qr_mixed_kernel(MixedArgs a) 
   double* mout = mred + kSmRed;
   double* mW = mout + kSmOut;
   double* mWp = mW + kSmW;
-  tree_climb(s, leaf, mT, mred, mout, mW, mWp);
+  if (s.climb) tree_climb(s, leaf, mT, mred, mout, mW, mWp);
 }
 
 // Per leaf: U_leaf = Q_leaf [B_leaf; 0] in FP32 on tcgen05 (panels last to
@@ -574,7 +574,9 @@ cudaError_t launch_tsqr_mixed(const TsqrState& s, char* extra, const void* X, in
   char* pb = t2 + align256(sizeof(double) * (size_t)s.P * npan * kNB2 * kNB2);
   MixedArgs a{s, (float*)extra, (double*)t2, (float*)pb, X, ldx, xtype, w, remove_mean, mean};
   leaf_qr_mixed_kernel<<<(unsigned)s.P, kMxThreads, kMixSmemTotal, st>>>(a);
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess || s.climb) return e;
+  return launch_tree_coop(s, st);
 }
 
 cudaError_t launch_modes_mixed(const TsqrState& s, char* extra, const double* Ur, int64_t ldur, int64_t r_fixed,
