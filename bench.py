@@ -211,6 +211,109 @@ def bench_mixed(args, dev):
     return out
 
 
+C3_N, C3_M, C3_RMAX = 10_000_000, 1808, 128
+
+
+def bench_waves_1808(args, dev):
+    """The 10,000,000 x 1808 float32 wake-like field (64 traveling waves,
+    power-law amplitudes, noise 1e-4; 72.3 GB) through the mixed path, timed,
+    and once through the FP64 path on the same X (the comparison the mixed
+    path is judged by).  99 % energy, at most 128 modes."""
+    import numpy as np
+    import torch
+    import paper_2405_15529_gb300 as pg
+    import synth
+    N, M, rmax = args.c3_rows, C3_M, C3_RMAX
+    XT = synth.waves_torch(N, M, 64, "powerlaw", 1e-4, 5, dev, dtype=torch.float32, row_chunk=1 << 18)
+    X = XT.t()
+    a, _, _ = synth.wave_params(64, "powerlaw")
+    s_cf = np.repeat(a * math.sqrt(N * M) / 2.0, 2)          # noise-free closed form (pairs)
+    noise_bound = 1e-4 * (math.sqrt(N) + math.sqrt(M))       # ~ ||noise||_2 (Weyl)
+
+    def run(prec, steps, warmup):
+        ws = torch.empty(pg.pod_workspace_size(N, M, 0, rmax, pg.F32, prec), dtype=torch.uint8, device=dev)
+        U = pg.empty_colmajor(N, rmax, torch.float32 if prec == pg.PREC_MIXED_3XTF32 else torch.float64, dev)
+        S = torch.empty(M, dtype=torch.float64, device=dev)
+        VT = pg.empty_colmajor(M, M, torch.float64, dev)
+        mean = torch.empty(N, dtype=torch.float64, device=dev)
+        r_dev = torch.zeros(1, dtype=torch.int64, device=dev)
+        out = (U, S, VT, mean, r_dev)
+        for _ in range(warmup):
+            pg.pod(X, remove_mean=True, energy=ENERGY, r_max=rmax, prec=prec, workspace=ws, out=out, check=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        pg.profile_begin(steps)
+        e0.record()
+        for _ in range(steps):
+            pg.pod(X, remove_mean=True, energy=ENERGY, r_max=rmax, prec=prec, workspace=ws, out=out, check=False)
+        e1.record()
+        torch.cuda.synchronize()
+        phases, n = pg.profile_end()
+        st, r, sweeps = pg.workspace_status(ws)
+        res = {"ms": e0.elapsed_time(e1) / steps, "status": st, "r": r, "sweeps": sweeps,
+               "phases_ms": {k: v / max(n, 1) for k, v in phases.items()}, "S": S.cpu().numpy()}
+        del ws, VT, mean, r_dev, S
+        torch.cuda.empty_cache()
+        return res, U
+
+    mix, Umix = run(pg.PREC_MIXED_3XTF32, args.c3_steps, 1)
+    f64, U64 = run(pg.PREC_FP64, 1, 0)
+    r = min(mix["r"], f64["r"])
+    G = torch.zeros((r, r), dtype=torch.float64, device=dev)
+    for r0 in range(0, N, 1 << 20):
+        G += Umix[r0:r0 + (1 << 20), :r].double().T @ U64[r0:r0 + (1 << 20), :r]
+    Gm = torch.zeros((r, r), dtype=torch.float64, device=dev)
+    for r0 in range(0, N, 1 << 20):
+        blk = Umix[r0:r0 + (1 << 20), :r].double()
+        Gm += blk.T @ blk
+    orth_mix = torch.linalg.norm(Gm - torch.eye(r, dtype=torch.float64, device=dev)).item()
+    # overlap of each mixed mode (pair subspace where the pair is unresolved) with the FP64 path's
+    Sm, S64 = mix["S"], f64["S"]
+    Gn = G.cpu().numpy()
+    worst = 1.0
+    i = 0
+    while i < r:
+        j = i + 1
+        while j < r and (S64[j - 1] - S64[j]) <= 1e-3 * S64[j - 1]:
+            j += 1
+        blk = Gn[i:j, i:j]
+        v = abs(blk[0, 0]) if j - i == 1 else float(np.linalg.svd(blk, compute_uv=False).min())
+        if S64[i] >= 1e-3 * S64[0]:
+            worst = min(worst, v)
+        i = j
+    del Umix, U64, G, Gm, X, XT
+    torch.cuda.empty_cache()
+    bytes_x = N * M * 4
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    tf32_3x = peaks.get("bf16_tflops", 1900.0) * 0.5 / 3.0     # nominal tf32/bf16 = 1/2; three MMAs per product
+    t_roof = max(bytes_x / (hbm * 1e9), 2.0 * N * M * M / (tf32_3x * 1e12))
+    leaf_ms = mix["phases_ms"]["leaf_qr_tree"]
+    return {"workload": f"waves64_powerlaw_{N}x{M}_f32_mean_removed_energy0.99_rmax{rmax}",
+            "status": [mix["status"], f64["status"]], "r": [mix["r"], f64["r"]],
+            "ms_per_step": mix["ms"], "steps": args.c3_steps, "warmup": 1,
+            "value": bytes_x / (mix["ms"] * 1e-3) / 1e9, "unit": "GB/s of X (float32)",
+            "phases_ms_per_step": mix["phases_ms"], "jacobi_sweeps": mix["sweeps"],
+            "fp64_path_ms_same_x": f64["ms"], "fp64_path_phases_ms": f64["phases_ms"],
+            "speedup_vs_fp64_path": f64["ms"] / mix["ms"],
+            "sigma_max_abs_diff_vs_fp64_path_over_smax": float(np.max(np.abs(Sm - S64)) / S64[0]),
+            "sigma_wave_pairs_max_abs_err_vs_noise_free_closed_form_over_smax":
+                float(np.max(np.abs(Sm[:128] - s_cf)) / s_cf[0]),
+            "noise_weyl_bound_over_smax": noise_bound / s_cf[0],
+            "min_mode_overlap_vs_fp64_path": worst, "mixed_U_orthonormality_fro": orth_mix,
+            "pct_roofline": {"value": t_roof / (mix["ms"] * 1e-3),
+                             "formula": "max(bytes_X/HBM_peak, 2NM^2/(tf32_peak/3)) / step time",
+                             "tf32_peak_tflops": peaks.get("bf16_tflops", 1900.0) * 0.5,
+                             "hbm_peak_gbs": hbm},
+            "leaf_kernel": {"kernel": "leaf_qr_mixed_kernel + tree_coop_kernel", "ms_per_step": leaf_ms,
+                            "useful_tflops": 2.0 * N * M * M / (leaf_ms * 1e-3) / 1e12}}
+
+
 def bench_spod(args, dev):
     """All 256 SPOD bins (complex64, N_f log-uniform in [2^16, 2^20], Nb_f in
     [16, 128]) in one persistent launch captured in a CUDA graph."""
@@ -430,6 +533,8 @@ def run_ours(args, rank, world, local_rank):
         extra["adjoint"] = bench_adjoint(args, dev)
     if world == 1 and not args.no_spod:
         extra["spod_batched"] = bench_spod(args, dev)
+    if world == 1 and not args.no_c3:
+        extra["mixed_waves_1808"] = bench_waves_1808(args, dev)
 
     levels = max(0, math.ceil(math.log2(P))) if P > 1 else 0
     launches_per_step = 1 + 3 + 1 + levels + 1   # leaf+tree, jacobi init/sweeps/finalize, root, tree levels, modes
@@ -476,6 +581,9 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-spod", action="store_true")
+    ap.add_argument("--no-c3", action="store_true", help="skip the 10,000,000 x 1808 mixed-vs-FP64 section")
+    ap.add_argument("--c3-rows", type=int, default=C3_N)
+    ap.add_argument("--c3-steps", type=int, default=1)
     ap.add_argument("--adj-steps", type=int, default=3)
     ap.add_argument("--spod-steps", type=int, default=3)
     ap.add_argument("--spod-bins", type=int, default=256)

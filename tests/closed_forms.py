@@ -41,6 +41,13 @@ def truncation_rank(M: int, decades: float, energy: float) -> int:
     return M
 
 
+def truncation_rank_of(s, energy: float) -> int:
+    """First r whose leading singular values s[:r] hold >= `energy` of
+    sum(s^2) (the cumulative-energy rule of Sec. 3.1, in plain FP64)."""
+    e = np.cumsum(np.asarray(s, dtype=np.float64) ** 2)
+    return int(np.argmax(e >= energy * e[-1])) + 1
+
+
 def sym2x2_eigs(a: float, b: float, c: float):
     """Eigenvalues of [[a, b], [b, c]] (quadratic formula)."""
     mid = 0.5 * (a + c)

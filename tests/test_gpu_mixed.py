@@ -89,3 +89,50 @@ def test_mixed_pod_full_size_fp32():
     G = res.U.double().T @ res.U.double()
     assert torch.linalg.norm(G - torch.eye(res.r, dtype=torch.float64, device="cuda")).item() < 1e-5
     _check_modes(res.U.double().cpu().numpy(), f64.U.cpu().numpy(), S64, res.r)
+
+
+def test_mixed_pod_full_size_waves_1808():
+    # 10,000,000 x 1808 float32 wake-like field: 64 traveling waves with
+    # power-law amplitudes, noise 1e-4, mean removed, 99 % energy, <= 128 modes
+    N, M, rmax = 10_000_000, 1808, 128
+    torch.cuda.empty_cache()
+    XT = synth.waves_torch(N, M, 64, "powerlaw", 1e-4, 5, "cuda", dtype=torch.float32, row_chunk=1 << 18)
+    X = XT.t()
+    mix = pg.pod(X, remove_mean=True, energy=0.99, r_max=rmax, prec=pg.PREC_MIXED_3XTF32)
+    S = mix.S.cpu().numpy()
+    U = mix.U
+    del mix
+    torch.cuda.empty_cache()
+    f64 = pg.pod(X, remove_mean=True, energy=0.99, r_max=rmax)
+    S64 = f64.S.cpu().numpy()
+    U64 = f64.U
+    r = f64.r
+    del f64
+    torch.cuda.empty_cache()
+    assert U.shape[1] == r
+    # mixed against the FP64 GPU path on the same X
+    assert np.max(np.abs(S - S64)) <= MIXED_SIGMA * S64[0], np.max(np.abs(S - S64)) / S64[0]
+    # both against the noise-free closed form a_j sqrt(NM)/2 (twice each), within
+    # the noise's spectral norm (Weyl), ~1e-4 (sqrt N + sqrt M)
+    a, _, _ = synth.wave_params(64, "powerlaw")
+    s_cf = np.repeat(a * np.sqrt(N * M) / 2.0, 2)
+    weyl = 1.5e-4 * (np.sqrt(N) + np.sqrt(M))
+    assert np.max(np.abs(S64[:128] - s_cf)) <= weyl
+    assert np.all(S64[128:] <= weyl)
+    assert r == cf.truncation_rank_of(s_cf, 0.99)
+    # orthonormal modes, and the same modes (pairs as subspaces) as the FP64 path
+    G = torch.zeros((r, r), dtype=torch.float64, device="cuda")
+    Gm = torch.zeros((r, r), dtype=torch.float64, device="cuda")
+    for r0 in range(0, N, 1 << 20):
+        blk = U[r0:r0 + (1 << 20)].double()
+        G += blk.T @ U64[r0:r0 + (1 << 20)]
+        Gm += blk.T @ blk
+    assert torch.linalg.norm(Gm - torch.eye(r, dtype=torch.float64, device="cuda")).item() < 1e-5
+    Gn = G.cpu().numpy()
+    for grp in parity.clusters(S64[:r]):
+        grp = [i for i in grp if S64[i] >= MODE_FLOOR * S64[0]]
+        if not grp:
+            continue
+        blk = Gn[np.ix_(grp, grp)]
+        v = abs(blk[0, 0]) if len(grp) == 1 else np.linalg.svd(blk, compute_uv=False).min()
+        assert v >= 1 - 1e-6, (grp, v)
