@@ -11,14 +11,19 @@ constexpr int kWarp = 32;
 
 // Header at the start of every workspace (512 bytes).  Each call clears it
 // with one cudaMemsetAsync before its first kernel.
+// The grid barrier's arrival counter and generation word sit in different
+// 128-byte lines, so the waiting blocks' polling does not contend with the
+// arrivals' atomics.
 struct WsHeader {
   int status;               // first device-side pylom_status raised (0 = OK)
   int sweeps;               // Jacobi sweeps used
   long long r;              // truncation rank chosen by pylom_pod
   unsigned barrier_count;   // grid barrier: arrivals
-  unsigned barrier_gen;     // grid barrier: generation
+  unsigned spare;
   unsigned rot[64];         // Jacobi: rotations performed in each sweep
-  unsigned char pad[512 - 24 - 64 * 4];
+  unsigned char pad0[384 - 24 - 64 * 4];
+  unsigned barrier_gen;     // grid barrier: generation (own line)
+  unsigned char pad1[512 - 384 - 4];
 };
 static_assert(sizeof(WsHeader) == 512, "workspace header must be 512 bytes");
 constexpr int kMaxSweeps = 64;
@@ -104,14 +109,17 @@ __device__ __forceinline__ bool grid_barrier(WsHeader* h, unsigned nblocks) {
         atomicAdd(&h->barrier_gen, 1u);
       } else {
         const unsigned long long t0 = global_ns();
+        unsigned polls = 0;
         while (ld_acquire_u32(&h->barrier_gen) == gen) {
-          if (global_ns() - t0 > kWaitLimitNs) {
-            raise_status(h, PYLOM_ERR_TIMEOUT);
-            ok = 0;
-            break;
+          if ((++polls & 63u) == 0) {
+            if (global_ns() - t0 > kWaitLimitNs) {
+              raise_status(h, PYLOM_ERR_TIMEOUT);
+              ok = 0;
+              break;
+            }
+            if (read_status(h) == PYLOM_ERR_TIMEOUT) { ok = 0; break; }
           }
-          if (read_status(h) == PYLOM_ERR_TIMEOUT) { ok = 0; break; }
-          __nanosleep(20);
+          __nanosleep(32);
         }
       }
       __threadfence();

@@ -44,10 +44,15 @@ __global__ void jacobi_init_kernel(SvdState s, const double* R, int64_t ldr) {
     s.V[idx] = (idx % Mp == idx / Mp) ? 1.0 : 0.0;
 }
 
+// EL = elements of a column per thread (M <= EL * kJacThreads): the pair's
+// two columns stay in registers between the dot products and the rotation,
+// so each step reads them from L2 once.
+template <int EL>
 __global__ void __launch_bounds__(kJacThreads) jacobi_kernel(SvdState s, int max_sweeps) {
   __shared__ double sred[3 * (kJacThreads / 32)];
   __shared__ double sout[4];
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tid = threadIdx.x;
+  constexpr int nthr = kJacThreads;
   const int64_t M = s.M, Mp = s.Mp, npairs = Mp / 2;
   const double tol = (double)M * 1.1102230246251565e-16;  // M * 2^-53
   int sweep = 0;
@@ -61,31 +66,75 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_kernel(SvdState s, int max
         const int64_t i = p < q ? p : q, j = p < q ? q : p;
         double* ai = s.A + i * M;
         double* aj = s.A + j * M;
-        double v[3] = {0.0, 0.0, 0.0};
-        for (int64_t r = tid; r < M; r += nthr) {
-          const double x = ldcg(ai + r), y = ldcg(aj + r);
-          v[0] += x * x;
-          v[1] += y * y;
-          v[2] += x * y;
+        double x[EL], y[EL];
+#pragma unroll
+        for (int e = 0; e < EL; ++e) {
+          const int64_t r = tid + (int64_t)e * nthr;
+          x[e] = (r < M) ? ldcg(ai + r) : 0.0;
+          y[e] = (r < M) ? ldcg(aj + r) : 0.0;
         }
-        block_sum<3>(v, sred, sout);
-        const double alpha = sout[0], beta = sout[1], gamma = sout[2];
-        if (gamma != 0.0 && fabs(gamma) > tol * sqrt(alpha * beta)) {
-          const double zeta = (beta - alpha) / (2.0 * gamma);
-          const double t = ((zeta >= 0.0) ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double c = 1.0 / sqrt(1.0 + t * t);
-          const double sn = c * t;
-          for (int64_t r = tid; r < M; r += nthr) {
-            const double x = ldcg(ai + r), y = ldcg(aj + r);
-            ai[r] = c * x - sn * y;
-            aj[r] = sn * x + c * y;
+        double v[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int e = 0; e < EL; ++e) {
+          v[0] += x[e] * x[e];
+          v[1] += y[e] * y[e];
+          v[2] += x[e] * y[e];
+        }
+        // block reduction (fixed order); thread 0 alone forms the rotation
+        // (FP64 square roots and divisions are slow on this part) and
+        // broadcasts it: sout = {c, s, rotate?}
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v[k] = warp_sum(v[k]);
+        if ((tid & 31) == 0) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) sred[k * (nthr / 32) + (tid >> 5)] = v[k];
+        }
+        __syncthreads();
+        if (tid == 0) {
+          double tot[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            double a = 0.0;
+            for (int w = 0; w < nthr / 32; ++w) a += sred[k * (nthr / 32) + w];
+            tot[k] = a;
+          }
+          const double alpha = tot[0], beta = tot[1], gamma = tot[2];
+          sout[2] = 0.0;
+          if (gamma != 0.0 && fabs(gamma) > tol * sqrt(alpha * beta)) {
+            const double zeta = (beta - alpha) / (2.0 * gamma);
+            const double t = ((zeta >= 0.0) ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            const double c = 1.0 / sqrt(1.0 + t * t);
+            sout[0] = c;
+            sout[1] = c * t;
+            sout[2] = 1.0;
+          }
+        }
+        __syncthreads();
+        if (sout[2] != 0.0) {
+          const double c = sout[0], sn = sout[1];
+#pragma unroll
+          for (int e = 0; e < EL; ++e) {
+            const int64_t r = tid + (int64_t)e * nthr;
+            if (r < M) {
+              ai[r] = c * x[e] - sn * y[e];
+              aj[r] = sn * x[e] + c * y[e];
+            }
           }
           double* vi = s.V + i * Mp;
           double* vj = s.V + j * Mp;
-          for (int64_t r = tid; r < Mp; r += nthr) {
-            const double x = ldcg(vi + r), y = ldcg(vj + r);
-            vi[r] = c * x - sn * y;
-            vj[r] = sn * x + c * y;
+#pragma unroll
+          for (int e = 0; e < EL; ++e) {
+            const int64_t r = tid + (int64_t)e * nthr;
+            x[e] = (r < Mp) ? ldcg(vi + r) : 0.0;
+            y[e] = (r < Mp) ? ldcg(vj + r) : 0.0;
+          }
+#pragma unroll
+          for (int e = 0; e < EL; ++e) {
+            const int64_t r = tid + (int64_t)e * nthr;
+            if (r < Mp) {
+              vi[r] = c * x[e] - sn * y[e];
+              vj[r] = sn * x[e] + c * y[e];
+            }
           }
           ++local_rot;
         }
@@ -241,7 +290,14 @@ cudaError_t launch_svd_fp64(const SvdState& s, const double* R, int64_t ldr, dou
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, kJacThreads, 0);
+  // smallest register footprint that holds a column (Mp <= EL * kJacThreads)
+  const void* kern;
+  if (s.Mp <= 1 * kJacThreads) kern = (const void*)jacobi_kernel<1>;
+  else if (s.Mp <= 2 * kJacThreads) kern = (const void*)jacobi_kernel<2>;
+  else if (s.Mp <= 4 * kJacThreads) kern = (const void*)jacobi_kernel<4>;
+  else if (s.Mp <= 8 * kJacThreads) kern = (const void*)jacobi_kernel<8>;
+  else kern = (const void*)jacobi_kernel<16>;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kJacThreads, 0);
   if (e != cudaSuccess) return e;
   int64_t grid = s.Mp / 2;
   const int64_t cap = (int64_t)nsm * (per_sm > 0 ? per_sm : 1);
@@ -250,7 +306,7 @@ cudaError_t launch_svd_fp64(const SvdState& s, const double* R, int64_t ldr, dou
   SvdState sa = s;
   int ms = max_sweeps;
   void* args[] = {(void*)&sa, (void*)&ms};
-  e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3((unsigned)grid), dim3(kJacThreads),
+  e = cudaLaunchCooperativeKernel(kern, dim3((unsigned)grid), dim3(kJacThreads),
                                   args, 0, st);
   if (e != cudaSuccess) return e;
   const size_t fsm = sizeof(double) * 2 * (size_t)s.M + sizeof(int) * (size_t)s.M;

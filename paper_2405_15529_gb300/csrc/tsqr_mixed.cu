@@ -84,22 +84,41 @@ struct KSum32 {
   __device__ __forceinline__ double get() const { return (double)s - (double)c; }
 };
 
-template <int K>
-__device__ __forceinline__ void block_sum_d(double (&v)[K], double* scratch, double* out) {
-  block_sum<K>(v, scratch, out);
+// Compensated FP32 value s + c (TwoSum addition): the cross-thread sums of
+// the panel statistics stay at about double-float accuracy without FP64
+// arithmetic, which runs at a small fraction of the FP32 rate on this part.
+struct F2 {
+  float s, c;
+};
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+  const float s = a.s + b.s;
+  const float bb = s - a.s;
+  const float e = (a.s - (s - bb)) + (b.s - bb);
+  return {s, e + a.c + b.c};
 }
 
-// Panel factorisation (columns [k, k+nbk) of the FP32 leaf), the same
-// two-pass-per-column scheme as the FP64 leaves: scale v_j and form its dot
-// products with the panel, then update the panel and the next norm.  Sums
-// are compensated FP32 per thread and FP64 across threads.
-// The passes run on a row-major copy of the panel (Pb: leaf rows k..h-1, 32
-// contiguous floats = 128 bytes per row), so every pass streams contiguous
-// rows instead of 32 columns that are N elements apart; the panel is
-// gathered before and scattered back to the column-major leaf after.
+// Single-pass panel factorisation (columns [k, k+nbk) of the FP32 leaf) on
+// the row-major panel copy Pb (leaf rows k..h-1, 32 floats = 128 bytes per
+// row).  Pass jj, over the rows from the previous diagonal on:
+//   - finishes column jj-1: scales its sub-diagonal into the reflector
+//     v_{jj-1} = u / (alpha - beta) and applies (I - tau v v^T) to the later
+//     panel columns;
+//   - forms, from the still unscaled column jj (u below the diagonal), the
+//     squared norm sum u_i^2 and the dots sum u_i a_ic with every other
+//     panel column, as compensated FP32 sums.
+// Warp 0 then forms beta, tau and the scale of column jj in FP64 and the
+// true dots v_j^T a_c = a_jc + scale * sum u_i a_ic (v_j has a one on the
+// diagonal), the forward recurrence of T, and the update factors
+// tau * v_j^T a_c for the next pass.  One pass and one reduction per column
+// (Householder convention beta = -sign(alpha) |x|, sign(0) = +1).
 __device__ void panel_factor_mixed(float* Y, int64_t ldy, int64_t k, int nbk, int64_t h, double* tau_out,
                                    double* sT, double* sred, double* sout, float* Pb) {
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = nthr >> 5;
+  float* spart = (float*)sred;     // [warp][32][2] partial sums (s, c)
+  float* srow = (float*)sout;      // [32] row j of the panel
+  float* sfc = srow + kNB2;        // [32] tau * v_j^T a_c (zero outside (jj, nbk))
+  float* sscale = sfc + kNB2;      // [1]  scale of column jj
   // gather: Pb[(i - k) * 32 + c] = Y[i, k + c] (zeros beyond nbk)
   for (int64_t i = k + tid; i < h; i += nthr) {
     float4* pr = (float4*)(Pb + (i - k) * kNB2);
@@ -113,110 +132,124 @@ __device__ void panel_factor_mixed(float* Y, int64_t ldy, int64_t k, int nbk, in
       pr[q] = v;
     }
   }
+  if (tid < kNB2) sfc[tid] = 0.f;
+  if (tid == 0) sscale[0] = 0.f;
   __syncthreads();
-  double xx;
-  {
-    KSum32 ks;
-    for (int64_t i = k + 1 + tid; i < h; i += nthr) {
-      const float a = Pb[(i - k) * kNB2];
-      ks.add(a * a);
-    }
-    double v[1] = {ks.get()};
-    block_sum_d<1>(v, sred, sout);
-    xx = sout[0];
-  }
   for (int jj = 0; jj < nbk; ++jj) {
     const int64_t j = k + jj;
-    const double alpha = (double)Pb[(j - k) * kNB2 + jj];
-    double tau_j = 0.0, beta = alpha, scale = 0.0;
-    if (xx != 0.0) {
-      const double nrm = sqrt(alpha * alpha + xx);
-      beta = (alpha >= 0.0) ? -nrm : nrm;
-      tau_j = (beta - alpha) / beta;
-      scale = 1.0 / (alpha - beta);
-    }
-    const float scf = (float)scale;
-    KSum32 acc[kNB2];
-    for (int64_t i = j + tid; i < h; i += nthr) {
+    float fc[kNB2];
+#pragma unroll
+    for (int c = 0; c < kNB2; ++c) fc[c] = sfc[c];
+    const float scp = sscale[0];
+    KSum32 acc[kNB2];   // acc[jj] collects sum u_i^2
+    for (int64_t i = (jj > 0 ? j - 1 : j) + tid; i < h; i += nthr) {
+      float4* pr = (float4*)(Pb + (i - k) * kNB2);
       float row[kNB2];
-      const float4* pr = (const float4*)(Pb + (i - k) * kNB2);
 #pragma unroll
       for (int q = 0; q < kNB2 / 4; ++q) {
         const float4 v4 = pr[q];
         row[4 * q] = v4.x; row[4 * q + 1] = v4.y; row[4 * q + 2] = v4.z; row[4 * q + 3] = v4.w;
       }
-      float rj = 0.f;   // row[jj] without a runtime index (keeps row[] in registers)
+      if (jj > 0) {
+        // row[jj - 1] re-read from the (L1-resident) row rather than indexed
+        // at run time, which would move row[] out of registers
+        const float rp = ((const float*)pr)[jj - 1];
+        const float v = (i == j - 1) ? 1.f : rp * scp;
+        // fc is zero outside (jj - 1, nbk), so the update needs no column test
 #pragma unroll
-      for (int c = 0; c < kNB2; ++c)
-        if (c == jj) rj = row[c];
-      float v = 1.f;
-      if (i != j) {
-        v = rj * scf;
-        Pb[(i - k) * kNB2 + jj] = v;
+        for (int c = 0; c < kNB2; ++c) row[c] = (c == jj - 1) ? (i > j - 1 ? v : row[c]) : row[c] - fc[c] * v;
       }
+      if (i == j) {
 #pragma unroll
-      for (int c = 0; c < kNB2; ++c)
-        if (c < nbk && c != jj) acc[c].add(v * row[c]);
-    }
-    double dv[kNB2];
+        for (int c = 0; c < kNB2; ++c) srow[c] = row[c];
+      } else if (i > j) {
+        float u = 0.f;
 #pragma unroll
-    for (int c = 0; c < kNB2; ++c) dv[c] = acc[c].get();
-    block_sum_d<kNB2>(dv, sred, sout);
-    if (tid == 0) {
-      Pb[(j - k) * kNB2 + jj] = (float)beta;
-      tau_out[jj] = tau_j;
-      for (int p = 0; p < jj; ++p) {
-        double s = 0.0;
-        for (int q = p; q < jj; ++q) s += sT[p * kNB2 + q] * sout[q];
-        sT[p * kNB2 + jj] = -tau_j * s;
-      }
-      sT[jj * kNB2 + jj] = tau_j;
-    }
-    float fc[kNB2];
-#pragma unroll
-    for (int c = 0; c < kNB2; ++c) fc[c] = (c > jj && c < nbk) ? (float)(tau_j * sout[c]) : 0.f;
-    KSum32 nx;
-    if (jj + 1 < nbk) {
-      for (int64_t i = j + tid; i < h; i += nthr) {
-        float4* pr = (float4*)(Pb + (i - k) * kNB2);
-        float row[kNB2];
-#pragma unroll
-        for (int q = 0; q < kNB2 / 4; ++q) {
-          const float4 v4 = pr[q];
-          row[4 * q] = v4.x; row[4 * q + 1] = v4.y; row[4 * q + 2] = v4.z; row[4 * q + 3] = v4.w;
-        }
-        float rj = 0.f;
+        for (int c = 0; c < kNB2; ++c) u = (c == jj) ? row[c] : u;
 #pragma unroll
         for (int c = 0; c < kNB2; ++c)
-          if (c == jj) rj = row[c];
-        const float v = (i == j) ? 1.f : rj;
-        float rn = 0.f;
-#pragma unroll
-        for (int c = 0; c < kNB2; ++c) {
-          if (c > jj) row[c] -= fc[c] * v;
-          if (c == jj + 1) rn = row[c];
-        }
-        if (i > j + 1) nx.add(rn * rn);
-        // write back the updated columns (the leading ones are unchanged)
+          if (c < nbk) acc[c].add(u * row[c]);
+      }
+      if (jj > 0) {
 #pragma unroll
         for (int q = 0; q < kNB2 / 4; ++q)
-          if (4 * q + 3 > jj) pr[q] = make_float4(row[4 * q], row[4 * q + 1], row[4 * q + 2], row[4 * q + 3]);
+          pr[q] = make_float4(row[4 * q], row[4 * q + 1], row[4 * q + 2], row[4 * q + 3]);
       }
     }
-    double nv[1] = {nx.get()};
-    block_sum_d<1>(nv, sred, sout);
-    xx = sout[0];
+    // block reduction of the 32 compensated sums: TwoSum shuffles, then the
+    // warps' partials in FP64 by warp 0 (lane c owns value c)
+#pragma unroll
+    for (int c = 0; c < kNB2; ++c) {
+      F2 v{acc[c].s, -acc[c].c};
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        F2 w{__shfl_xor_sync(0xffffffffu, v.s, o), __shfl_xor_sync(0xffffffffu, v.c, o)};
+        v = f2_add(v, w);
+      }
+      if (lane == 0) {
+        spart[(warp * kNB2 + c) * 2] = v.s;
+        spart[(warp * kNB2 + c) * 2 + 1] = v.c;
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const int c = lane;
+      double tot = 0.0;
+      for (int w = 0; w < nwarps; ++w)
+        tot += (double)spart[(w * kNB2 + c) * 2] + (double)spart[(w * kNB2 + c) * 2 + 1];
+      const double xx = __shfl_sync(0xffffffffu, tot, jj);
+      double tau_j = 0.0, beta = 0.0, scale = 0.0;
+      if (lane == 0) {
+        const double alpha = (double)srow[jj];
+        beta = alpha;
+        if (xx != 0.0) {
+          const double nrm = sqrt(alpha * alpha + xx);
+          beta = (alpha >= 0.0) ? -nrm : nrm;
+          tau_j = (beta - alpha) / beta;
+          scale = 1.0 / (alpha - beta);
+        }
+      }
+      tau_j = __shfl_sync(0xffffffffu, tau_j, 0);
+      scale = __shfl_sync(0xffffffffu, scale, 0);
+      // w_c = v_j^T a_c (c > jj) or v_c^T v_j (c < jj)
+      const double wcv = (c < nbk && c != jj) ? (double)srow[c] + scale * tot : 0.0;
+      // T[0:jj, jj] = -tau T[0:jj, 0:jj] w[0:jj]; lane p owns row p
+      double tp = 0.0;
+      for (int q = 0; q < jj; ++q) {
+        const double wq = __shfl_sync(0xffffffffu, wcv, q);
+        if (c <= q) tp += sT[c * kNB2 + q] * wq;
+      }
+      if (c < jj) sT[c * kNB2 + jj] = -tau_j * tp;
+      if (c == jj) {
+        sT[jj * kNB2 + jj] = tau_j;
+        tau_out[jj] = tau_j;
+      }
+      sfc[c] = (c > jj && c < nbk) ? (float)(tau_j * wcv) : 0.f;
+      if (lane == 0) {
+        sscale[0] = (float)scale;
+        Pb[(j - k) * kNB2 + jj] = (float)beta;
+      }
+    }
+    __syncthreads();
   }
-  // scatter the factored panel (R above the diagonal, reflectors below) back
+  // scatter the factored panel back; the last column's sub-diagonal still
+  // needs its scale
+  const float scl = sscale[0];
   for (int64_t i = k + tid; i < h; i += nthr) {
     const float4* pr = (const float4*)(Pb + (i - k) * kNB2);
 #pragma unroll
     for (int q = 0; q < kNB2 / 4; ++q) {
       const float4 v = pr[q];
-      if (4 * q + 0 < nbk) Y[i + (k + 4 * q + 0) * ldy] = v.x;
-      if (4 * q + 1 < nbk) Y[i + (k + 4 * q + 1) * ldy] = v.y;
-      if (4 * q + 2 < nbk) Y[i + (k + 4 * q + 2) * ldy] = v.z;
-      if (4 * q + 3 < nbk) Y[i + (k + 4 * q + 3) * ldy] = v.w;
+#define PYLOM_SCATTER_ONE(t, e)                                                   \
+  {                                                                               \
+    const int c = 4 * q + (t);                                                    \
+    if (c < nbk) Y[i + (k + c) * ldy] = (c == nbk - 1 && i > k + c) ? (e) * scl : (e); \
+  }
+      PYLOM_SCATTER_ONE(0, v.x)
+      PYLOM_SCATTER_ONE(1, v.y)
+      PYLOM_SCATTER_ONE(2, v.z)
+      PYLOM_SCATTER_ONE(3, v.w)
+#undef PYLOM_SCATTER_ONE
     }
   }
   __syncthreads();
@@ -242,6 +275,11 @@ __device__ __forceinline__ void issue_3xtf32(uint32_t d_hh, uint32_t d_x, unsign
 // The block-reflector application on tcgen05.  C: leaf-relative FP32 matrix
 // (rows r0..h, ld ldc), ncols columns.  TRANS: op(T) = T^T (factorisation) or
 // T (modes).  Returns false on a timed-out wait.
+// Software pipelining: the global loads of the next W-stage step (and of the
+// next C-stage row tile's reflector rows) are issued before waiting on the
+// current MMAs, and the C-stage epilogue loads the next 16-column group of C
+// while it adds the current one, so the tensor-core work and the folds
+// overlap the memory latency.
 template <bool TRANS>
 __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int nbk, int64_t h, float* C,
                                    int64_t ldc, int ncols, const double* sT, unsigned char* smem, uint32_t tmem,
@@ -260,41 +298,37 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
 #pragma unroll
     for (int p = 0; p < kNB2; ++p) ws_[p] = wc_[p] = 0.f;
     const int64_t nkc = (L + kKC - 1) / kKC;
+    // A = C^T chunk: row = column c (0..127), K = row i (0..31); warp w
+    // takes columns c = w + 4u, lane = row.  B = V: row = reflector p, K = row i.
+    float xa[kCH / 4], xb[8];
+    auto load_w = [&](int64_t kc) {
+      const int64_t row = k + kc * kKC + lane;
+      const bool rok = row < h;
+#pragma unroll
+      for (int u = 0; u < kCH / 4; ++u) {
+        const int c = warp + 4 * u;
+        xa[u] = (rok && c < wc) ? C[row + (int64_t)(c0 + c) * ldc] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) xb[u] = vval_f(Y, ldy, k, nbk, h, row, warp + 4 * u);
+    };
+    load_w(0);
     for (int64_t kc = 0; kc < nkc && ok; ++kc) {
-      const int64_t rb = k + kc * kKC;
-      // A = C^T chunk: row = column c (0..127), K = row i (0..31); warp w
-      // takes columns c = w + 4u, lane = row; 8 loads in flight per batch
-      {
-        const int64_t row = rb + lane;
-        const bool rok = row < h;
-        for (int cb = 0; cb < kCH; cb += 32) {
-          float x[8];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int c = cb + warp + 4 * u;
-            x[u] = (rok && c < wc) ? C[row + (int64_t)(c0 + c) * ldc] : 0.f;
-          }
+      for (int u = 0; u < kCH / 4; ++u) {
+        float hi, lo;
+        split_tf32(xa[u], hi, lo);
+        const uint32_t o = cm_off(warp + 4 * u, lane, kKC);
+        *(float*)(smem + kOffA + o) = hi;
+        *(float*)(smem + kOffAlo + o) = lo;
+      }
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            float hi, lo;
-            split_tf32(x[u], hi, lo);
-            const uint32_t o = cm_off(cb + warp + 4 * u, lane, kKC);
-            *(float*)(smem + kOffA + o) = hi;
-            *(float*)(smem + kOffAlo + o) = lo;
-          }
-        }
-        // B = V chunk: row = reflector p (0..31), K = row i
-        float x[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) x[u] = vval_f(Y, ldy, k, nbk, h, rb + lane, warp + 4 * u);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          float hi, lo;
-          split_tf32(x[u], hi, lo);
-          const uint32_t o = cm_off(warp + 4 * u, lane, kKC);
-          *(float*)(smem + kOffB + o) = hi;
-          *(float*)(smem + kOffBlo + o) = lo;
-        }
+      for (int u = 0; u < 8; ++u) {
+        float hi, lo;
+        split_tf32(xb[u], hi, lo);
+        const uint32_t o = cm_off(warp + 4 * u, lane, kKC);
+        *(float*)(smem + kOffB + o) = hi;
+        *(float*)(smem + kOffBlo + o) = lo;
       }
       fence_smem_async();
       fence_before();
@@ -304,12 +338,14 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
         issue_3xtf32(tmem, tmem + kNB2, smem, kKC, idesc_tf32(128, kNB2));
         commit(mbar);
       }
+      if (kc + 1 < nkc) load_w(kc + 1);   // in flight while the MMAs run
       const bool w_ok = mbar_wait(mbar, phase);
       phase ^= 1u;
       fence_after();
       ok = !__syncthreads_or(!w_ok);
       if (!ok) break;
       const uint32_t lanebase = (uint32_t)(warp * 32) << 16;
+#pragma unroll
       for (int p0 = 0; p0 < kNB2; p0 += 16) {
         float hh[16], xx[16];
         tmem_ld16(tmem + lanebase + (uint32_t)p0, hh);
@@ -322,10 +358,12 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
           ws_[p0 + j] = t;
         }
       }
+      // the next step's MMAs overwrite the accumulators only after the
+      // barrier that follows its shared-memory stores
       fence_before();
-      __syncthreads();
     }
     if (!ok) break;
+    __syncthreads();
     {
       const int c = warp * 32 + lane;
 #pragma unroll
@@ -349,19 +387,21 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
     }
     // ---- C stage: per 128-row tile, P = V_tile W'; C += P ----
     const int64_t nrt = (L + kRT - 1) / kRT;
+    float xv[kNB2];
+    auto load_v = [&](int64_t rt) {
+      const int64_t row = k + rt * kRT + tid;
+#pragma unroll
+      for (int p = 0; p < kNB2; ++p) xv[p] = vval_f(Y, ldy, k, nbk, h, row, p);
+    };
+    load_v(0);
     for (int64_t rt = 0; rt < nrt && ok; ++rt) {
       const int64_t rb = k + rt * kRT;
-      // A = V rows: row = r (0..127), K = p (0..31); thread t takes row t,
-      // all 32 loads issued before use
       {
         const int r = tid;
-        float x[kNB2];
-#pragma unroll
-        for (int p = 0; p < kNB2; ++p) x[p] = vval_f(Y, ldy, k, nbk, h, rb + r, p);
 #pragma unroll
         for (int p = 0; p < kNB2; ++p) {
           float hi, lo;
-          split_tf32(x[p], hi, lo);
+          split_tf32(xv[p], hi, lo);
           const uint32_t o = cm_off(r, p, kNB2);
           *(float*)(smem + kOffA + o) = hi;
           *(float*)(smem + kOffAlo + o) = lo;
@@ -375,29 +415,41 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
         issue_3xtf32(tmem, tmem + kCH, smem, kNB2, idesc_tf32(128, kCH));
         commit(mbar);
       }
+      if (rt + 1 < nrt) load_v(rt + 1);
+      const int64_t row = rb + warp * 32 + lane;
+      const bool rok = row < h;
+      float* crow = C + row + (int64_t)c0 * ldc;
+      float cv[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) cv[j] = (rok && j < wc) ? crow[(int64_t)j * ldc] : 0.f;
       const bool w_ok = mbar_wait(mbar, phase);
       phase ^= 1u;
       fence_after();
       ok = !__syncthreads_or(!w_ok);
       if (!ok) break;
-      const int64_t row = rb + warp * 32 + lane;
-      float v[16], vx[16];
       for (int cc = 0; cc < kCH; cc += 16) {
+        float cn[16];
+        if (cc + 16 < kCH) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            cn[j] = (rok && cc + 16 + j < wc) ? crow[(int64_t)(cc + 16 + j) * ldc] : 0.f;
+        }
+        float v[16], vx[16];
         tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, v);
         tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(kCH + cc), vx);
-        if (row < h) {
-          float cv[16];
+        if (rok) {
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            cv[j] = (cc + j < wc) ? C[row + (int64_t)(c0 + cc + j) * ldc] : 0.f;
+            if (cc + j < wc) crow[(int64_t)(cc + j) * ldc] = cv[j] + (v[j] + vx[j]);
+        }
+        if (cc + 16 < kCH) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (cc + j < wc) C[row + (int64_t)(c0 + cc + j) * ldc] = cv[j] + (v[j] + vx[j]);
+          for (int j = 0; j < 16; ++j) cv[j] = cn[j];
         }
       }
       fence_before();
-      __syncthreads();
     }
+    __syncthreads();
   }
   return ok;
 }
