@@ -79,7 +79,8 @@ const char* pylom_last_error(void);
 
 /* Number of TSQR leaves for an N-row problem with leaf height hint
  * leaf_rows = b: P = max(1, floor(N / b)); leaf_rows = 0 picks
- * P = max(1, min(304, floor(N / max(M, 1024)))).  Leaf i owns rows
+ * P = max(1, min(304, floor(N / max(M, 1024)))) (the FP64 path; the mixed
+ * path of pylom_pod caps the automatic choice at 152, one leaf per SM).  Leaf i owns rows
  * [floor(i N / P), floor((i+1) N / P)), so every leaf has >= M rows.
  * Returns -1 on invalid arguments. */
 int64_t pylom_leaf_count(int64_t N, int64_t M, int64_t leaf_rows);

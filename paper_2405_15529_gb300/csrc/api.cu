@@ -27,19 +27,21 @@ pylom_status cuda_fail(cudaError_t e, const char* where) {
 }
 
 constexpr int64_t kMaxM = 4096;        // shared-memory bound of the tree merge and finalize
-constexpr int64_t kAutoLeaves = 304;   // two leaves per SM of a 152-SM GB300
+constexpr int64_t kAutoLeaves = 304;       // FP64 path: two leaves per SM of a 152-SM GB300
+constexpr int64_t kAutoLeavesMixed = 152;  // mixed path: one leaf (512 tensor-memory columns) per SM
 constexpr int64_t kMinAutoLeafRows = 1024;
 
 // P = max(1, floor(N / b)) for a given leaf height b; automatic choice:
-// P = min(304, floor(N / max(M, 1024))), at least 1.
-int64_t leaves_of(int64_t N, int64_t M, int64_t leaf_rows) {
+// P = min(304, floor(N / max(M, 1024))) (152 for the mixed path), at least 1.
+int64_t leaves_of(int64_t N, int64_t M, int64_t leaf_rows, int prec = PYLOM_PREC_FP64) {
   int64_t P;
   if (leaf_rows > 0) {
     P = N / leaf_rows;
   } else {
     const int64_t b = M > kMinAutoLeafRows ? M : kMinAutoLeafRows;
+    const int64_t cap = (prec == PYLOM_PREC_MIXED_3XTF32) ? kAutoLeavesMixed : kAutoLeaves;
     P = N / b;
-    if (P > kAutoLeaves) P = kAutoLeaves;
+    if (P > cap) P = cap;
   }
   return P < 1 ? 1 : P;
 }
@@ -113,7 +115,7 @@ extern "C" size_t pylom_pod_workspace_size(int64_t N, int64_t M, int64_t leaf_ro
   if (!tall_shape_ok(N, M, leaf_rows) || r_max < 1 || r_max > M) return 0;
   if (xtype != PYLOM_F32 && xtype != PYLOM_F64) return 0;
   if (prec != PYLOM_PREC_FP64 && prec != PYLOM_PREC_MIXED_3XTF32) return 0;
-  return pod_bytes(N, M, leaves_of(N, M, leaf_rows), r_max, prec);
+  return pod_bytes(N, M, leaves_of(N, M, leaf_rows, prec), r_max, prec);
 }
 
 extern "C" pylom_status pylom_pod(const void* X, int64_t N, int64_t M, int64_t ldx, int xtype,
@@ -138,7 +140,7 @@ extern "C" pylom_status pylom_pod(const void* X, int64_t N, int64_t M, int64_t l
   if (r_max < 1 || r_max > M) return fail(PYLOM_ERR_SHAPE, "pylom_pod: r_max must be in [1, M]");
   if (ldx < N || ldu < N || ldvt < M) return fail(PYLOM_ERR_ARG, "pylom_pod: leading dimension too small");
   const bool mixed = prec == PYLOM_PREC_MIXED_3XTF32;
-  const int64_t P = leaves_of(N, M, leaf_rows);
+  const int64_t P = leaves_of(N, M, leaf_rows, prec);
   const size_t need = pod_bytes(N, M, P, r_max, prec);
   if (!aligned256(ws) || ws_bytes < need)
     return fail(PYLOM_ERR_WORKSPACE, "pylom_pod: workspace needs %zu bytes, 256-byte aligned (got %zu)",

@@ -35,7 +35,22 @@ struct SvdState {
   int64_t M, Mp;            // size, padded to even
   double* A;                // M x Mp working columns
   double* V;                // Mp x Mp accumulated rotations
+  // binary32 preconditioning (M >= kJac32MinM only, else null)
+  int64_t Mb;               // columns padded to a multiple of two blocks
+  float* A32;               // M x Mb
+  float* V32;               // Mb x Mb
+  double* G;                // Mp x Mp Newton-Schulz scratch
+  double* Tm;               // Mp x Mp Newton-Schulz scratch
+  unsigned* rot32;          // rotations per binary32 sweep
+  double* mmws;             // split-K scratch of the binary64 products
 };
+
+// From this size on, binary32 block-Jacobi sweeps precondition the binary64
+// one-sided Jacobi of the small SVD (svd_jacobi32.cu).
+constexpr int64_t kJac32MinM = 512;
+size_t jacobi32_extra_bytes(int64_t M);
+void jacobi32_carve(SvdState& s, char* p);
+cudaError_t launch_jacobi32_precondition(const SvdState& s, const double* R, int64_t ldr, cudaStream_t st);
 
 // with_y: include the N x M FP64 working copy (the FP64 path; the mixed
 // path keeps an FP32 copy in its own extra region instead)

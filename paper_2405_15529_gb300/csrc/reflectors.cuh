@@ -188,14 +188,25 @@ static __device__ void merge_panel_factor(double* Rt, double* Rb, int64_t M, int
   }
   for (int jj = 0; jj < nbk; ++jj) {
     const int64_t c = k + jj;
-    const double alpha = ldcg(Rt + c + c * M);
-    double tau_c = 0.0, beta = alpha, scale = 0.0;
-    if (xx != 0.0) {
-      const double nrm = sqrt(alpha * alpha + xx);
-      beta = (alpha >= 0.0) ? -nrm : nrm;
-      tau_c = (beta - alpha) / beta;
-      scale = 1.0 / (alpha - beta);
+    // thread 0 forms the reflector's scalars (FP64 square roots and divisions
+    // are slow on this part; every thread repeating them cost more than the
+    // column's dot products) and broadcasts them
+    if (tid == 0) {
+      const double alpha = ldcg(Rt + c + c * M);
+      double tau0 = 0.0, beta0 = alpha, scale0 = 0.0;
+      if (xx != 0.0) {
+        const double nrm = sqrt(alpha * alpha + xx);
+        beta0 = (alpha >= 0.0) ? -nrm : nrm;
+        tau0 = (beta0 - alpha) / beta0;
+        scale0 = 1.0 / (alpha - beta0);
+      }
+      sd[kNB - 3] = tau0;
+      sd[kNB - 2] = beta0;
+      sd[kNB - 1] = scale0;
     }
+    __syncthreads();
+    const double tau_c = sd[kNB - 3], beta = sd[kNB - 2], scale = sd[kNB - 1];
+    __syncthreads();
     // pass A: u_c = scale * bottom column c; dots of u_c with the bottom part
     // of the later panel columns (q > jj) and with earlier reflectors (q < jj)
     double acc[kNB];

@@ -23,7 +23,8 @@ constexpr int kFinThreads = 1024;
 
 size_t svd_state_bytes(int64_t M) {
   const int64_t Mp = M + (M & 1);
-  return align256(sizeof(double) * (size_t)M * Mp) + align256(sizeof(double) * (size_t)Mp * Mp);
+  return align256(sizeof(double) * (size_t)M * Mp) + align256(sizeof(double) * (size_t)Mp * Mp) +
+         jacobi32_extra_bytes(M);
 }
 
 void svd_state_carve(SvdState& s, char* base, int64_t M) {
@@ -31,6 +32,12 @@ void svd_state_carve(SvdState& s, char* base, int64_t M) {
   s.Mp = M + (M & 1);
   s.A = (double*)base;
   s.V = (double*)(base + align256(sizeof(double) * (size_t)M * s.Mp));
+  s.Mb = 0;
+  s.A32 = s.V32 = nullptr;
+  s.G = s.Tm = s.mmws = nullptr;
+  s.rot32 = nullptr;
+  if (M >= kJac32MinM)
+    jacobi32_carve(s, (char*)s.V + align256(sizeof(double) * (size_t)s.Mp * s.Mp));
 }
 
 __global__ void jacobi_init_kernel(SvdState s, const double* R, int64_t ldr) {
@@ -282,8 +289,13 @@ __global__ void __launch_bounds__(kFinThreads) svd_finalize_kernel(SvdState s, d
 cudaError_t launch_svd_fp64(const SvdState& s, const double* R, int64_t ldr, double* U, int64_t ldu,
                             double* S, double* VT, int64_t ldvt, int max_sweeps, double energy,
                             int64_t r_max, cudaStream_t st) {
-  jacobi_init_kernel<<<64, 256, 0, st>>>(s, R, ldr);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  if (s.M >= kJac32MinM) {
+    e = launch_jacobi32_precondition(s, R, ldr, st);
+  } else {
+    jacobi_init_kernel<<<64, 256, 0, st>>>(s, R, ldr);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 0, per_sm = 0;
   e = cudaGetDevice(&dev);

@@ -10,17 +10,19 @@
 // A block-reflector application C := (I - V op(T) V^T) C runs per chunk of
 // up to 128 columns of C:
 //   W stage:  W^T (128 x 32) = C_chunk^T V   -- MMA M = 128 columns,
-//             N = 32 reflectors, K = the rows, 32 rows per shared-memory stage;
+//             N = 32 reflectors, K = the rows, 64 rows per shared-memory step;
 //   W' = -op(T) W  (FP64 on CUDA cores, split into hi/lo);
-//   C stage:  per 128-row tile, P (128 x 128) = V_tile W' -- M = 128 rows,
-//             N = 128 columns, K = 32 reflectors; each thread adds its row of
-//             P (read from tensor memory) to C.
-// One thread issues the MMAs and commits them to an mbarrier; every wait is
-// time-bounded (PYLOM_ERR_TIMEOUT) and tensor memory is freed on every exit.
+//   C stage:  per 256-row tile, two MMAs P (128 x 128) = V_half W' -- M = 128
+//             rows, N = 128 columns, K = 32 reflectors; each thread adds its
+//             row of P (read from tensor memory) to C.
+// One CTA of 8 warps per SM owns all 512 tensor-memory columns (warps w and
+// w + 4 read lane quadrant w % 4).  One thread issues the MMAs and commits
+// them to an mbarrier; every wait is time-bounded (PYLOM_ERR_TIMEOUT) and
+// tensor memory is freed on every exit.
 //
 // Accumulation: long chains of MMAs into one tensor-memory accumulator drift
 // (every accumulate step of the tensor core rounds, and the errors do not
-// cancel), so every 32-row stage of the W stage writes fresh accumulators
+// cancel), so every 64-row step of the W stage writes fresh accumulators
 // that the threads fold into compensated FP32 sums, and the hi*hi products
 // and the small hi*lo + lo*hi cross terms go to separate accumulators that
 // are added on the CUDA cores.
@@ -31,25 +33,32 @@
 namespace pylom {
 
 constexpr int kNB2 = 32;          // panel width
-constexpr int kMxThreads = 128;   // 4 warps = the 4 tensor-memory lane quadrants
+constexpr int kMxThreads = 256;   // 8 warps; warps w and w + 4 share tensor-memory lane quadrant w % 4
 constexpr int kCH = 128;          // column chunk
-constexpr int kRT = 128;          // row tile (C stage)
-constexpr int kKC = 32;           // rows per W-stage shared-memory stage
-constexpr uint32_t kTmemCols = 256;   // C stage: hi*hi and cross-term accumulators, 128 columns each
+constexpr int kKC = 64;           // rows per W-stage step (MMA K)
+constexpr int kRT = 256;          // rows per C-stage tile (two 128-row MMAs)
+constexpr uint32_t kTmemCols = 512;   // C stage: two halves x (hi*hi, cross) x 128 columns
 
-// shared-memory plan (bytes)
-constexpr int kTileA = kCH * kKC * 4;           // 16 KB: one 128 x 32 fp32 tile
-constexpr int kOffA = 0;                        // A hi (W stage: C^T chunk; C stage: V rows)
-constexpr int kOffAlo = kOffA + kTileA;         // A lo
-constexpr int kOffB = kOffAlo + kTileA;         // B hi (W stage: V 32 x 32 uses 4 KB; C stage: W'^T 128 x 32)
-constexpr int kOffBlo = kOffB + kTileA;         // B lo
-constexpr int kOffW = kOffBlo + kTileA;         // W: 32 x 128 fp32 (16 KB)
-constexpr int kOffT = kOffW + kNB2 * kCH * 4;   // T: 32 x 32 fp64 (8 KB)
-constexpr int kOffRed = kOffT + kNB2 * kNB2 * 8;  // reductions: 32 x 4 warps doubles + 64 outputs
-constexpr int kMixSmem = kOffRed + (kNB2 * 4 + 64) * 8;
+// shared-memory plan (bytes); the W-stage and C-stage operands share [0, kOpBytes)
+constexpr int kWA = kCH * kKC * 4;                 // 32 KB: W-stage A (C^T chunk, 128 x 64)
+constexpr int kWB = kNB2 * kKC * 4;                // 8 KB:  W-stage B (V, 32 x 64)
+constexpr int kOffWA = 0, kOffWAlo = kWA, kOffWB = 2 * kWA, kOffWBlo = 2 * kWA + kWB;
+constexpr int kCA = 128 * kNB2 * 4;                // 16 KB: C-stage A half (V rows, 128 x 32)
+constexpr int kOffCA = 0;                          // hi halves at 0, kCA; lo halves at 2 kCA, 3 kCA
+constexpr int kOffCB = 4 * kCA, kOffCBlo = 5 * kCA;  // C-stage B (W'^T, 128 x 32)
+constexpr int kOpBytes = 6 * kCA;                  // 96 KB >= the W stage's 80 KB
+static_assert(2 * kWA + 2 * kWB <= kOpBytes, "W-stage operands must fit the operand region");
+constexpr int kOffW = kOpBytes;                    // W: 32 x 128 fp32 (16 KB)
+constexpr int kOffT = kOffW + kNB2 * kCH * 4;      // T: 32 x 32 fp64 (8 KB)
+constexpr int kOffRed = kOffT + kNB2 * kNB2 * 8;   // panel reductions: 8 warps x 32 x (s, c) floats
+constexpr int kOffOut = kOffRed + 8 * kNB2 * 2 * 4;  // panel broadcasts (512 bytes)
+constexpr int kMixSmem = kOffOut + 512;
 // the FP64 tree merge reuses the same buffer with the leaf kernel's plan
 constexpr int kMergeSmem = (int)kLeafSmemBytes;
 constexpr int kMixSmemTotal = kMixSmem > kMergeSmem ? kMixSmem : kMergeSmem;
+// a second CTA on the same SM would wait for the first one's tensor memory:
+// the shared-memory plan keeps them apart
+static_assert(2 * kMixSmemTotal > 228 * 1024, "mixed-leaf CTAs must not share an SM");
 
 struct MixedArgs {
   TsqrState s;
@@ -255,14 +264,14 @@ __device__ void panel_factor_mixed(float* Y, int64_t ldy, int64_t k, int nbk, in
   __syncthreads();
 }
 
-// Issue the K-slices of a 3xTF32 product from the four shared tiles (rows
-// of Kk elements): hi*hi into d_hh, hi*lo + lo*hi into d_x, both starting
-// from zero.
-__device__ __forceinline__ void issue_3xtf32(uint32_t d_hh, uint32_t d_x, unsigned char* smem, int Kk,
-                                             uint32_t idesc) {
+// Issue the K-slices of a 3xTF32 product from four shared tiles (byte
+// offsets; rows of Kk elements): hi*hi into d_hh, hi*lo + lo*hi into d_x,
+// both starting from zero.
+__device__ __forceinline__ void issue_3xtf32(uint32_t d_hh, uint32_t d_x, unsigned char* smem, int oa, int oalo,
+                                             int ob, int oblo, int Kk, uint32_t idesc) {
   using namespace tc05;
-  const uint32_t a_hi = smem_u32(smem + kOffA), a_lo = smem_u32(smem + kOffAlo);
-  const uint32_t b_hi = smem_u32(smem + kOffB), b_lo = smem_u32(smem + kOffBlo);
+  const uint32_t a_hi = smem_u32(smem + oa), a_lo = smem_u32(smem + oalo);
+  const uint32_t b_hi = smem_u32(smem + ob), b_lo = smem_u32(smem + oblo);
   const uint32_t sbo = (uint32_t)(Kk / 4) * 128, lbo = 128;
   for (int kk = 0; kk < Kk / 8; ++kk) {
     const uint32_t o = (uint32_t)kk * 256;
@@ -286,31 +295,33 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
                                    uint64_t* mbar, uint32_t& phase) {
   using namespace tc05;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int quad = warp & 3, half = warp >> 2;       // tensor-memory lane quadrant; which half of the work
+  const uint32_t lanebase = (uint32_t)(quad * 32) << 16;
   float* sW = (float*)(smem + kOffW);
   const int64_t L = h - k;
   bool ok = true;
   for (int c0 = 0; c0 < ncols && ok; c0 += kCH) {
     const int wc = min(kCH, ncols - c0);
     // ---- W stage: W^T (128 x 32) = C_chunk^T V over all rows ----
-    // thread (warp w, lane l) owns column c = 32 w + l of the chunk and folds
-    // each stage's partial W[0..31][c] into compensated FP32 sums
-    float ws_[kNB2], wc_[kNB2];
+    // thread (quad, half, lane) folds W[16 half .. 16 half + 15][32 quad + lane]
+    float ws_[16], wc_[16];
 #pragma unroll
-    for (int p = 0; p < kNB2; ++p) ws_[p] = wc_[p] = 0.f;
+    for (int p = 0; p < 16; ++p) ws_[p] = wc_[p] = 0.f;
     const int64_t nkc = (L + kKC - 1) / kKC;
-    // A = C^T chunk: row = column c (0..127), K = row i (0..31); warp w
-    // takes columns c = w + 4u, lane = row.  B = V: row = reflector p, K = row i.
-    float xa[kCH / 4], xb[8];
+    // loads: thread t takes row t % 64 of the step and columns (reflectors)
+    // t / 64 + 4 u; consecutive lanes read consecutive rows
+    const int lr = tid & (kKC - 1), lg = tid / kKC;
+    float xa[kCH / 4], xb[kNB2 / 4];
     auto load_w = [&](int64_t kc) {
-      const int64_t row = k + kc * kKC + lane;
+      const int64_t row = k + kc * kKC + lr;
       const bool rok = row < h;
 #pragma unroll
       for (int u = 0; u < kCH / 4; ++u) {
-        const int c = warp + 4 * u;
+        const int c = lg + 4 * u;
         xa[u] = (rok && c < wc) ? C[row + (int64_t)(c0 + c) * ldc] : 0.f;
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) xb[u] = vval_f(Y, ldy, k, nbk, h, row, warp + 4 * u);
+      for (int u = 0; u < kNB2 / 4; ++u) xb[u] = vval_f(Y, ldy, k, nbk, h, row, lg + 4 * u);
     };
     load_w(0);
     for (int64_t kc = 0; kc < nkc && ok; ++kc) {
@@ -318,24 +329,24 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
       for (int u = 0; u < kCH / 4; ++u) {
         float hi, lo;
         split_tf32(xa[u], hi, lo);
-        const uint32_t o = cm_off(warp + 4 * u, lane, kKC);
-        *(float*)(smem + kOffA + o) = hi;
-        *(float*)(smem + kOffAlo + o) = lo;
+        const uint32_t o = cm_off(lg + 4 * u, lr, kKC);
+        *(float*)(smem + kOffWA + o) = hi;
+        *(float*)(smem + kOffWAlo + o) = lo;
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < kNB2 / 4; ++u) {
         float hi, lo;
         split_tf32(xb[u], hi, lo);
-        const uint32_t o = cm_off(warp + 4 * u, lane, kKC);
-        *(float*)(smem + kOffB + o) = hi;
-        *(float*)(smem + kOffBlo + o) = lo;
+        const uint32_t o = cm_off(lg + 4 * u, lr, kKC);
+        *(float*)(smem + kOffWB + o) = hi;
+        *(float*)(smem + kOffWBlo + o) = lo;
       }
       fence_smem_async();
       fence_before();
       __syncthreads();
       fence_after();
       if (tid == 0) {
-        issue_3xtf32(tmem, tmem + kNB2, smem, kKC, idesc_tf32(128, kNB2));
+        issue_3xtf32(tmem, tmem + kNB2, smem, kOffWA, kOffWAlo, kOffWB, kOffWBlo, kKC, idesc_tf32(128, kNB2));
         commit(mbar);
       }
       if (kc + 1 < nkc) load_w(kc + 1);   // in flight while the MMAs run
@@ -344,18 +355,16 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
       fence_after();
       ok = !__syncthreads_or(!w_ok);
       if (!ok) break;
-      const uint32_t lanebase = (uint32_t)(warp * 32) << 16;
-#pragma unroll
-      for (int p0 = 0; p0 < kNB2; p0 += 16) {
+      {
         float hh[16], xx[16];
-        tmem_ld16(tmem + lanebase + (uint32_t)p0, hh);
-        tmem_ld16(tmem + lanebase + (uint32_t)(kNB2 + p0), xx);
+        tmem_ld16(tmem + lanebase + (uint32_t)(16 * half), hh);
+        tmem_ld16(tmem + lanebase + (uint32_t)(kNB2 + 16 * half), xx);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const float y = (hh[j] + xx[j]) - wc_[p0 + j];
-          const float t = ws_[p0 + j] + y;
-          wc_[p0 + j] = (t - ws_[p0 + j]) - y;
-          ws_[p0 + j] = t;
+          const float y = (hh[j] + xx[j]) - wc_[j];
+          const float t = ws_[j] + y;
+          wc_[j] = (t - ws_[j]) - y;
+          ws_[j] = t;
         }
       }
       // the next step's MMAs overwrite the accumulators only after the
@@ -365,9 +374,9 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
     if (!ok) break;
     __syncthreads();
     {
-      const int c = warp * 32 + lane;
+      const int c = quad * 32 + lane;
 #pragma unroll
-      for (int p = 0; p < kNB2; ++p) sW[p * kCH + c] = (float)((double)ws_[p] - (double)wc_[p]);
+      for (int j = 0; j < 16; ++j) sW[(16 * half + j) * kCH + c] = (float)((double)ws_[j] - (double)wc_[j]);
     }
     __syncthreads();
     // ---- W' = -op(T) W, as B = W'^T (row = column c, K = p), split ----
@@ -382,10 +391,10 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
       float hi, lo;
       split_tf32((float)(-s), hi, lo);
       const uint32_t o = cm_off(c, p, kNB2);
-      *(float*)(smem + kOffB + o) = hi;
-      *(float*)(smem + kOffBlo + o) = lo;
+      *(float*)(smem + kOffCB + o) = hi;
+      *(float*)(smem + kOffCBlo + o) = lo;
     }
-    // ---- C stage: per 128-row tile, P = V_tile W'; C += P ----
+    // ---- C stage: per 256-row tile, P = V_tile W' (two 128-row MMAs); C += P ----
     const int64_t nrt = (L + kRT - 1) / kRT;
     float xv[kNB2];
     auto load_v = [&](int64_t rt) {
@@ -397,14 +406,14 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
     for (int64_t rt = 0; rt < nrt && ok; ++rt) {
       const int64_t rb = k + rt * kRT;
       {
-        const int r = tid;
+        const int hv = tid >> 7, r = tid & 127;   // half of the tile, row within it
 #pragma unroll
         for (int p = 0; p < kNB2; ++p) {
           float hi, lo;
           split_tf32(xv[p], hi, lo);
           const uint32_t o = cm_off(r, p, kNB2);
-          *(float*)(smem + kOffA + o) = hi;
-          *(float*)(smem + kOffAlo + o) = lo;
+          *(float*)(smem + kOffCA + hv * kCA + o) = hi;
+          *(float*)(smem + kOffCA + (2 + hv) * kCA + o) = lo;
         }
       }
       fence_smem_async();
@@ -412,13 +421,17 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
       __syncthreads();
       fence_after();
       if (tid == 0) {
-        issue_3xtf32(tmem, tmem + kCH, smem, kNB2, idesc_tf32(128, kCH));
+#pragma unroll
+        for (int hv = 0; hv < 2; ++hv)
+          issue_3xtf32(tmem + hv * 256, tmem + hv * 256 + kCH, smem, kOffCA + hv * kCA, kOffCA + (2 + hv) * kCA,
+                       kOffCB, kOffCBlo, kNB2, idesc_tf32(128, kCH));
         commit(mbar);
       }
       if (rt + 1 < nrt) load_v(rt + 1);
-      const int64_t row = rb + warp * 32 + lane;
+      const int64_t row = rb + 128 * half + 32 * quad + lane;
       const bool rok = row < h;
       float* crow = C + row + (int64_t)c0 * ldc;
+      const uint32_t tbase = tmem + lanebase + (uint32_t)(half * 256);
       float cv[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) cv[j] = (rok && j < wc) ? crow[(int64_t)j * ldc] : 0.f;
@@ -435,8 +448,8 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
             cn[j] = (rok && cc + 16 + j < wc) ? crow[(int64_t)(cc + 16 + j) * ldc] : 0.f;
         }
         float v[16], vx[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, v);
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(kCH + cc), vx);
+        tmem_ld16(tbase + (uint32_t)cc, v);
+        tmem_ld16(tbase + (uint32_t)(kCH + cc), vx);
         if (rok) {
 #pragma unroll
           for (int j = 0; j < 16; ++j)
@@ -497,7 +510,7 @@ __global__ void __launch_bounds__(kMxThreads) leaf_qr_mixed_kernel(MixedArgs a) 
   float* Y = a.Yf + r0;
   double* sT = (double*)(msm + kOffT);
   double* sred = (double*)(msm + kOffRed);
-  double* sout = sred + kNB2 * 4;
+  double* sout = (double*)(msm + kOffOut);
   if (a.xtype == PYLOM_F32)
     mixed_prologue<float>(a, Y, ldy, r0, h);
   else
