@@ -206,7 +206,9 @@ pylom_status pylom_svd_small(const double* R, int64_t M, int64_t ldr, double* U,
  * Three steps, so the launch can be captured in a CUDA graph:
  *   plan  (host only): bin sizes N[f] x Nb[f] (1 <= Nb <= 128, N >= Nb),
  *         optional per-bin leaf heights (NULL or <= 0: built-in choice, an
- *         autotuner may supply them), kmodes (0..32 modes returned per bin,
+ *         autotuner may supply them; leaves never exceed 1024 rows for
+ *         complex64 or 512 for complex128 -- a bin is split into more
+ *         leaves where needed), kmodes (0..32 modes returned per bin,
  *         capped at Nb), prec: PYLOM_PREC_FP64 (complex128 leaves) or
  *         PYLOM_PREC_MIXED_3XTF32 (complex64 leaves with compensated FP32
  *         sums; tree, Jacobi and R always binary64).  Returns an opaque plan

@@ -19,6 +19,8 @@
 // Precision: the leaf working copy is complex64 (TC = float, the "mixed"
 // path: FP32 storage and updates, compensated FP32 sums reduced in FP64) or
 // complex128 (TC = double); tree, Jacobi and all reflector scalars are FP64.
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace pylom {
@@ -99,6 +101,73 @@ struct KSum {
   }
 };
 
+// Warp total of a compensated complex sum times a complex FP64 factor, in
+// the working precision.  TC = float: the lanes combine their (sum,
+// compensation) pairs by TwoSum in FP32 and lane 0 alone forms factor *
+// total in FP64 and broadcasts it (FP64 arithmetic runs at a small fraction
+// of the FP32 rate on this part, so per-lane FP64 reductions dominated the
+// complex64 leaves).  TC = double: the plain FP64 reduction.
+__device__ __forceinline__ void two_sum_f(float& s, float& c, float os, float oc) {
+  const float t = s + os;
+  const float bb = t - s;
+  const float e = (s - (t - bb)) + (os - bb);
+  s = t;
+  c = c + oc + e;
+}
+template <typename TC>
+__device__ __forceinline__ TCx<TC> warp_ksum_scaled(const KSum<TC>& k, double2 factor);
+template <>
+__device__ __forceinline__ TCx<float> warp_ksum_scaled<float>(const KSum<float>& k, double2 factor) {
+  float sx = k.sx, cx = -k.cx, sy = k.sy, cy = -k.cy;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float osx = __shfl_xor_sync(0xffffffffu, sx, o), ocx = __shfl_xor_sync(0xffffffffu, cx, o);
+    const float osy = __shfl_xor_sync(0xffffffffu, sy, o), ocy = __shfl_xor_sync(0xffffffffu, cy, o);
+    two_sum_f(sx, cx, osx, ocx);
+    two_sum_f(sy, cy, osy, ocy);
+  }
+  float fx = 0.f, fy = 0.f;
+  if ((threadIdx.x & 31) == 0) {
+    const double2 f = cmul(factor, make_double2((double)sx + (double)cx, (double)sy + (double)cy));
+    fx = (float)f.x;
+    fy = (float)f.y;
+  }
+  return {__shfl_sync(0xffffffffu, fx, 0), __shfl_sync(0xffffffffu, fy, 0)};
+}
+template <>
+__device__ __forceinline__ TCx<double> warp_ksum_scaled<double>(const KSum<double>& k, double2 factor) {
+  const double2 f = cmul(factor, warp_csum(k.get()));
+  return {f.x, f.y};
+}
+
+// Block total of the real part of a compensated sum, valid in thread 0
+// (scratch: one double2 per warp).
+template <typename TC>
+__device__ __forceinline__ double block_real_sum0(const KSum<TC>& k, double2* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  if (sizeof(TC) == 4) {
+    float s = (float)k.sx, c = -(float)k.cx;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float os = __shfl_xor_sync(0xffffffffu, s, o), oc = __shfl_xor_sync(0xffffffffu, c, o);
+      two_sum_f(s, c, os, oc);
+    }
+    __syncthreads();
+    if (lane == 0) scratch[warp] = make_double2((double)s, (double)c);
+  } else {
+    double v = (double)k.sx - (double)k.cx;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) scratch[warp] = make_double2(v, 0.0);
+  }
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < nwarps; ++w) t += scratch[w].x + scratch[w].y;
+  return t;
+}
+
 // ---------------------------------------------------------------------------
 // per-bin description and workspace tables (built by the host plan)
 // ---------------------------------------------------------------------------
@@ -113,6 +182,7 @@ struct BinDesc {
   int64_t arr_off;   // unsigned: P arrival counters
   int64_t jac_off;   // double2: 2 x Np x Np, Np = Nb rounded up to even (Jacobi A = R^H, V)
   int64_t ur_off;    // double2: Nb x Nb left vectors of R (sorted, phased)
+  int64_t rf_off;    // float2: P x Nb x Nb complex64 copies of the node reflectors (complex64 leaves only)
   int64_t s_off;     // S output offset
   float2* U;         // output modes, N x k complex64
   int64_t ldu;
@@ -132,6 +202,7 @@ struct BatchArgs {
   int nD;
   void* ybase;          // TC complex working copies
   double2* zbase;       // FP64 complex tables
+  float2* fbase;        // complex64 copies of the node reflectors (complex64 leaves only)
   unsigned* ubase;      // counters
   double* S;            // packed singular values
   double2* scratch;     // per block: 2 x kMaxNb x kMaxK
@@ -141,6 +212,14 @@ struct BatchArgs {
 constexpr int kBThreads = 256;
 constexpr int kMaxNb = 128;
 constexpr int kMaxK = 32;
+// Leaves hold at most 32 rows per lane (complex64) or 16 (complex128), so a
+// warp keeps a whole leaf column in registers between its dot product with
+// the current reflector and its update.
+constexpr int64_t kLeafMaxRowsF = 1024;
+constexpr int64_t kLeafMaxRowsD = 512;
+template <typename TC> struct LeafCap;
+template <> struct LeafCap<float> { static constexpr int EL = 32; };
+template <> struct LeafCap<double> { static constexpr int EL = 16; };
 
 __device__ __forceinline__ int64_t bin_leaf_begin(const BinDesc& b, int64_t leaf) {
   return (leaf * b.N) / b.P;
@@ -164,7 +243,7 @@ __device__ __forceinline__ double2 block_csum(double2 v, double2* sred) {
 // ---------------------------------------------------------------------------
 template <typename TC>
 __device__ void leaf_qr_complex(const BatchArgs& a, const BinDesc& b, int64_t leaf, double2* sd,
-                                double2* sred) {
+                                double2* sred, typename CT<TC>::V* sv) {
   using V = typename CT<TC>::V;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
@@ -189,40 +268,66 @@ __device__ void leaf_qr_complex(const BatchArgs& a, const BinDesc& b, int64_t le
       const TCx<TC> y = CT<TC>::ldt(Y + i + j * ldy);
       ks.add(y.x * y.x + y.y * y.y, (TC)0);
     }
-    const double xx = block_csum(ks.get(), sred).x;
-    const double2 alpha = CT<TC>::ld(Y + j + j * ldy);
-    double2 t = make_double2(0.0, 0.0), scale = make_double2(0.0, 0.0);
-    double beta = alpha.x;
-    if (!(xx == 0.0 && alpha.y == 0.0)) {
-      const double nrm = sqrt(cabs2(alpha) + xx);
-      beta = (alpha.x >= 0.0) ? -nrm : nrm;
-      t = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
-      scale = cdiv(make_double2(1.0, 0.0), make_double2(alpha.x - beta, alpha.y));
+    // thread 0 forms the reflector's scalars and broadcasts them
+    const double xx0 = block_real_sum0<TC>(ks, sred);
+    if (tid == 0) {
+      const double2 alpha = CT<TC>::ld(Y + j + j * ldy);
+      double2 t0 = make_double2(0.0, 0.0), scale0 = make_double2(0.0, 0.0);
+      double beta0 = alpha.x;
+      if (!(xx0 == 0.0 && alpha.y == 0.0)) {
+        const double nrm = sqrt(cabs2(alpha) + xx0);
+        beta0 = (alpha.x >= 0.0) ? -nrm : nrm;
+        t0 = make_double2((beta0 - alpha.x) / beta0, -alpha.y / beta0);
+        scale0 = cdiv(make_double2(1.0, 0.0), make_double2(alpha.x - beta0, alpha.y));
+      }
+      sd[0] = t0;
+      sd[1] = scale0;
+      sd[2] = make_double2(beta0, 0.0);
     }
+    __syncthreads();
+    const double2 t = sd[0], scale = sd[1];
+    const double beta = sd[2].x;
     const TCx<TC> sc = tc_of<TC>(scale);
-    for (int64_t i = j + 1 + tid; i < h; i += nthr)
-      CT<TC>::stt(Y + i + j * ldy, tc_mul(CT<TC>::ldt(Y + i + j * ldy), sc));
+    // scaled reflector v_j (one on the diagonal) into the leaf and the stage
+    for (int64_t i = j + tid; i < h; i += nthr) {
+      TCx<TC> v = {(TC)1, (TC)0};
+      if (i > j) {
+        v = tc_mul(CT<TC>::ldt(Y + i + j * ldy), sc);
+        CT<TC>::stt(Y + i + j * ldy, v);
+      }
+      CT<TC>::stt(sv + i, v);
+    }
     __syncthreads();
     if (tid == 0) {
       CT<TC>::st(Y + j + j * ldy, make_double2(beta, 0.0));
       tau[j] = t;
     }
     if (j + 1 < Nb && (t.x != 0.0 || t.y != 0.0)) {
-      // d_c = v_j^H y_c for c > j (a warp per column), then
+      // a warp per column c > j, held in registers: d_c = v_j^H y_c, then
       // y_c -= conj(tau) d_c v_j
-      const TCx<TC> one = {(TC)1, (TC)0};
+      constexpr int EL = LeafCap<TC>::EL;
       for (int64_t c = j + 1 + warp; c < Nb; c += nwarps) {
+        V* yc = Y + c * ldy;
+        TCx<TC> x[EL];
         KSum<TC> kd;
-        for (int64_t i = j + lane; i < h; i += 32) {
-          const TCx<TC> v = (i == j) ? one : CT<TC>::ldt(Y + i + j * ldy);
-          const TCx<TC> p = tc_mulc(v, CT<TC>::ldt(Y + i + c * ldy));
-          kd.add(p.x, p.y);
+#pragma unroll
+        for (int e = 0; e < EL; ++e) {
+          const int64_t i = j + lane + 32 * e;
+          x[e] = (i < h) ? CT<TC>::ldt(yc + i) : TCx<TC>{(TC)0, (TC)0};
         }
-        const double2 d = warp_csum(kd.get());
-        const TCx<TC> f = tc_of<TC>(cmul(cconj(t), d));
-        for (int64_t i = j + lane; i < h; i += 32) {
-          const TCx<TC> v = (i == j) ? one : CT<TC>::ldt(Y + i + j * ldy);
-          CT<TC>::stt(Y + i + c * ldy, tc_sub(CT<TC>::ldt(Y + i + c * ldy), tc_mul(f, v)));
+#pragma unroll
+        for (int e = 0; e < EL; ++e) {
+          const int64_t i = j + lane + 32 * e;
+          if (i < h) {
+            const TCx<TC> p = tc_mulc(CT<TC>::ldt(sv + i), x[e]);
+            kd.add(p.x, p.y);
+          }
+        }
+        const TCx<TC> f = warp_ksum_scaled<TC>(kd, cconj(t));
+#pragma unroll
+        for (int e = 0; e < EL; ++e) {
+          const int64_t i = j + lane + 32 * e;
+          if (i < h) CT<TC>::stt(yc + i, tc_sub(x[e], tc_mul(f, CT<TC>::ldt(sv + i))));
         }
       }
     }
@@ -234,52 +339,150 @@ __device__ void leaf_qr_complex(const BatchArgs& a, const BinDesc& b, int64_t le
     const int64_t i = idx % Nb, c = idx / Nb;
     Rl[idx] = (i <= c) ? CT<TC>::ld(Y + i + c * ldy) : make_double2(0.0, 0.0);
   }
-  (void)sd;
 }
 
 // QR of [Rt; Rb] (two upper-triangular Nb x Nb, FP64 complex): reflector c
-// is [e_c; u_c] with u_c in column c of Rb (rows 0..c); H_c^H applied to the
-// trailing columns.  A warp per trailing column.
-__device__ void tree_merge_complex(double2* Rt, double2* Rb, double2* tau, int64_t Nb, double2* sd) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  for (int64_t c = 0; c < Nb; ++c) {
-    if (warp == 0) {
-      double xx = 0.0;
-      for (int64_t i = lane; i <= c; i += 32) xx += cabs2(__ldcg(Rb + i + c * Nb));
-      xx = warp_sum(xx);
-      if (lane == 0) {
-        const double2 alpha = __ldcg(Rt + c + c * Nb);
-        double2 t = make_double2(0.0, 0.0), scale = make_double2(0.0, 0.0);
-        double beta = alpha.x;
-        if (!(xx == 0.0 && alpha.y == 0.0)) {
-          const double nrm = sqrt(cabs2(alpha) + xx);
-          beta = (alpha.x >= 0.0) ? -nrm : nrm;
-          t = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
-          scale = cdiv(make_double2(1.0, 0.0), make_double2(alpha.x - beta, alpha.y));
+// is [e_c; u_c] with u_c in column c of Rb (rows 0..c), H_c = I - t_c v v^H;
+// H_c^H is applied to the trailing columns.  Blocked by panels of kMP
+// columns: within a panel one reflector at a time (a warp per later panel
+// column); the trailing columns then take the panel's block reflector
+// Q = I - V T V^H (T by the forward recurrence) as W = V^H C, W' = T^H W,
+// C -= V W' with one thread per entry, so the dot products need no
+// cross-lane reductions (FP64 runs at a small fraction of the FP32 rate on
+// this part).  sm: shared scratch of kMergeSmem double2.
+constexpr int kMP = 8;
+constexpr int kMergeSmem = kMaxNb * kMP + kMP * kMaxNb + kMP * kMP;
+__device__ void tree_merge_complex(double2* Rt, double2* Rb, double2* tau, int64_t Nb, double2* sd,
+                                   float2* Rbf, double2* sm) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5, nthr = blockDim.x;
+  double2* sU = sm;                       // [i][p]: u of the panel's reflector p, rows 0..Nb-1
+  double2* sW = sU + kMaxNb * kMP;        // [p][column]
+  double2* sT = sW + kMP * kMaxNb;        // [q][p], upper
+  for (int64_t k = 0; k < Nb; k += kMP) {
+    const int nbk = (int)((Nb - k) < kMP ? (Nb - k) : kMP);
+    for (int idx = tid; idx < kMaxNb * kMP; idx += nthr) sU[idx] = make_double2(0.0, 0.0);
+    for (int idx = tid; idx < kMP * kMP; idx += nthr) sT[idx] = make_double2(0.0, 0.0);
+    __syncthreads();
+    for (int jj = 0; jj < nbk; ++jj) {
+      const int64_t c = k + jj;
+      if (warp == 0) {
+        double xx = 0.0;
+        for (int64_t i = lane; i <= c; i += 32) xx += cabs2(__ldcg(Rb + i + c * Nb));
+        xx = warp_sum(xx);
+        if (lane == 0) {
+          const double2 alpha = __ldcg(Rt + c + c * Nb);
+          double2 t = make_double2(0.0, 0.0), scale = make_double2(0.0, 0.0);
+          double beta = alpha.x;
+          if (!(xx == 0.0 && alpha.y == 0.0)) {
+            const double nrm = sqrt(cabs2(alpha) + xx);
+            beta = (alpha.x >= 0.0) ? -nrm : nrm;
+            t = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
+            scale = cdiv(make_double2(1.0, 0.0), make_double2(alpha.x - beta, alpha.y));
+          }
+          sd[0] = t;
+          sd[1] = scale;
+          Rt[c + c * Nb] = make_double2(beta, 0.0);
+          tau[c] = t;
+          sT[jj * kMP + jj] = t;
         }
-        sd[0] = t;
-        sd[1] = scale;
-        Rt[c + c * Nb] = make_double2(beta, 0.0);
-        tau[c] = t;
+      }
+      __syncthreads();
+      const double2 t = sd[0], scale = sd[1];
+      for (int64_t i = tid; i <= c; i += nthr) {
+        const double2 u = cmul(__ldcg(Rb + i + c * Nb), scale);
+        Rb[i + c * Nb] = u;
+        sU[i * kMP + jj] = u;
+      }
+      __syncthreads();
+      if (t.x != 0.0 || t.y != 0.0) {
+        // the later columns of this panel, one reflector at a time
+        for (int64_t cc = c + 1 + warp; cc < k + nbk; cc += nwarps) {
+          double2 s = make_double2(0.0, 0.0);
+          for (int64_t i = lane; i <= c; i += 32) s = cadd(s, cmulc(sU[i * kMP + jj], __ldcg(Rb + i + cc * Nb)));
+          s = cadd(warp_csum(s), __ldcg(Rt + c + cc * Nb));
+          const double2 f = cmul(cconj(t), s);
+          for (int64_t i = lane; i <= c; i += 32)
+            Rb[i + cc * Nb] = csub(__ldcg(Rb + i + cc * Nb), cmul(f, sU[i * kMP + jj]));
+          __syncwarp();
+          if (lane == 0) Rt[c + cc * Nb] = csub(__ldcg(Rt + c + cc * Nb), f);
+        }
+      }
+      __syncthreads();
+    }
+    const int64_t c1 = k + nbk;   // first trailing column
+    if (c1 >= Nb) break;
+    // T[0:j, j] = -t_j T[0:j, 0:j] (V^H v_j)[0:j]; v_q^H v_j = u_q^H u_j (the
+    // e parts are disjoint); a warp per pair (q, j), then warp 0 forms T
+    for (int pr = warp; pr < nbk * nbk; pr += nwarps) {
+      const int q = pr % nbk, j = pr / nbk;
+      if (q >= j) continue;
+      double2 s = make_double2(0.0, 0.0);
+      for (int64_t i = lane; i <= k + q; i += 32) s = cadd(s, cmulc(sU[i * kMP + q], sU[i * kMP + j]));
+      s = warp_csum(s);
+      if (lane == 0) sW[q * kMaxNb + j] = s;   // staging (sW is free until the trailing update)
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int j = 1; j < nbk; ++j) {
+        const double2 tj = sT[j * kMP + j];
+        for (int p = 0; p < j; ++p) {
+          double2 acc = make_double2(0.0, 0.0);
+          for (int q = p; q < j; ++q) acc = cadd(acc, cmul(sT[p * kMP + q], sW[q * kMaxNb + j]));
+          sT[p * kMP + j] = cmul(make_double2(-tj.x, -tj.y), acc);
+        }
       }
     }
     __syncthreads();
-    const double2 t = sd[0], scale = sd[1];
-    for (int64_t i = tid; i <= c; i += blockDim.x) Rb[i + c * Nb] = cmul(__ldcg(Rb + i + c * Nb), scale);
+    // W[p][cc] = Rt[k+p][cc] + sum_{i <= k+p} conj(u_p[i]) Rb[i][cc]
+    const int64_t ncols = Nb - c1;
+    for (int64_t idx = tid; idx < nbk * ncols; idx += nthr) {
+      const int p = (int)(idx % nbk);
+      const int64_t cc = c1 + idx / nbk;
+      double2 s = __ldcg(Rt + (k + p) + cc * Nb);
+      for (int64_t i = 0; i <= k + p; ++i) s = cadd(s, cmulc(sU[i * kMP + p], __ldcg(Rb + i + cc * Nb)));
+      sW[p * kMaxNb + (cc - c1)] = s;
+    }
     __syncthreads();
-    if (t.x != 0.0 || t.y != 0.0) {
-      for (int64_t cc = c + 1 + warp; cc < Nb; cc += nwarps) {
-        double2 s = make_double2(0.0, 0.0);
-        for (int64_t i = lane; i <= c; i += 32) s = cadd(s, cmulc(__ldcg(Rb + i + c * Nb), __ldcg(Rb + i + cc * Nb)));
-        s = cadd(warp_csum(s), __ldcg(Rt + c + cc * Nb));
-        const double2 f = cmul(cconj(t), s);
-        for (int64_t i = lane; i <= c; i += 32)
-          Rb[i + cc * Nb] = csub(__ldcg(Rb + i + cc * Nb), cmul(f, __ldcg(Rb + i + c * Nb)));
-        __syncwarp();
-        if (lane == 0) Rt[c + cc * Nb] = csub(__ldcg(Rt + c + cc * Nb), f);
+    // W' = T^H W, in place column by column (row p needs rows q <= p)
+    for (int64_t cc = tid; cc < ncols; cc += nthr) {
+      double2 w[kMP];
+#pragma unroll
+      for (int q = 0; q < kMP; ++q) w[q] = (q < nbk) ? sW[q * kMaxNb + cc] : make_double2(0.0, 0.0);
+#pragma unroll
+      for (int p = 0; p < kMP; ++p) {
+        if (p >= nbk) break;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int q = 0; q <= p; ++q) acc = cadd(acc, cmul(cconj(sT[q * kMP + p]), w[q]));
+        sW[p * kMaxNb + cc] = acc;
       }
     }
     __syncthreads();
+    // C -= V W': top rows k..k+nbk-1 of Rt, rows 0..k+nbk-1 of Rb
+    for (int64_t idx = tid; idx < nbk * ncols; idx += nthr) {
+      const int p = (int)(idx % nbk);
+      const int64_t cc = c1 + idx / nbk;
+      double2* rt = Rt + (k + p) + cc * Nb;
+      *rt = csub(__ldcg(rt), sW[p * kMaxNb + (cc - c1)]);
+    }
+    for (int64_t idx = tid; idx < c1 * ncols; idx += nthr) {
+      const int64_t i = idx % c1, cc = c1 + idx / c1;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int p = 0; p < nbk; ++p) acc = cadd(acc, cmul(sU[i * kMP + p], sW[p * kMaxNb + (cc - c1)]));
+      double2* rb = Rb + i + cc * Nb;
+      *rb = csub(__ldcg(rb), acc);
+    }
+    __syncthreads();
+  }
+  // complex64 copy of the node reflectors (rows 0..c of column c) for the
+  // leaves' single-precision walk down the tree
+  if (Rbf) {
+    for (int64_t idx = threadIdx.x; idx < Nb * Nb; idx += blockDim.x) {
+      const int64_t i = idx % Nb, c = idx / Nb;
+      if (i <= c) {
+        const double2 v = __ldcg(Rb + idx);
+        Rbf[idx] = make_float2((float)v.x, (float)v.y);
+      }
+    }
   }
 }
 
@@ -399,40 +602,70 @@ __device__ void bin_jacobi(const BatchArgs& a, const BinDesc& b, double2* sd, in
 // phase D: modes of one leaf
 // ---------------------------------------------------------------------------
 template <typename TC>
-__device__ void leaf_modes_complex(const BatchArgs& a, const BinDesc& b, int64_t leaf, double2* scratch) {
+__device__ void leaf_modes_complex(const BatchArgs& a, const BinDesc& b, int64_t leaf, double2* scratch,
+                                   typename CT<TC>::V* sv) {
   using V = typename CT<TC>::V;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int64_t Nb = b.Nb, k = b.k, P = b.P;
-  double2* Bt = scratch;                 // Nb x k
-  double2* Bb = scratch + kMaxNb * kMaxK;
   const double2* UR = a.zbase + b.ur_off;
-  for (int64_t idx = tid; idx < Nb * k; idx += blockDim.x) Bt[idx] = UR[(idx % Nb) + (idx / Nb) * Nb];
-  __syncthreads();
-  // walk the tree from the root to this leaf
   int64_t top = 1;
   while (top * 2 < P) top *= 2;
   int64_t node = 0;
+  // B at the leaf (Nb x k, complex TC): the first k columns of U_R pushed
+  // down the tree from the root to this leaf
+  using TB = typename std::conditional<sizeof(TC) == 4, float2, double2>::type;
+  TB* Bt = (TB*)scratch;
+  TB* Bb = Bt + kMaxNb * kMaxK;
+  for (int64_t idx = tid; idx < Nb * k; idx += blockDim.x) {
+    const double2 v = UR[(idx % Nb) + (idx / Nb) * Nb];
+    if constexpr (sizeof(TC) == 4) Bt[idx] = make_float2((float)v.x, (float)v.y);
+    else Bt[idx] = v;
+  }
+  __syncthreads();
   for (int64_t step = (P > 1 ? top : 0); step >= 1; step >>= 1) {
     const int64_t right = node + step;
     if (right >= P) continue;
     const bool go_right = leaf >= right;
-    const double2* Uu = a.zbase + b.rs_off + right * Nb * Nb;
     const double2* tau = a.zbase + b.taut_off + right * Nb;
-    for (int64_t idx = tid; idx < Nb * k; idx += blockDim.x) Bb[idx] = make_double2(0.0, 0.0);
+    for (int64_t idx = tid; idx < Nb * k; idx += blockDim.x) {
+      if constexpr (sizeof(TC) == 4) Bb[idx] = make_float2(0.f, 0.f);
+      else Bb[idx] = make_double2(0.0, 0.0);
+    }
     __syncthreads();
     for (int64_t col = warp; col < k; col += nwarps) {
-      double2* bt = Bt + col * Nb;
-      double2* bb = Bb + col * Nb;
+      TB* bt = Bt + col * Nb;
+      TB* bb = Bb + col * Nb;
       for (int64_t c = Nb - 1; c >= 0; --c) {
         const double2 t = tau[c];
         if (t.x == 0.0 && t.y == 0.0) continue;
-        double2 s = make_double2(0.0, 0.0);
-        for (int64_t i = lane; i <= c; i += 32) s = cadd(s, cmulc(Uu[i + c * Nb], bb[i]));
-        s = cadd(warp_csum(s), bt[c]);
-        const double2 f = cmul(t, s);
-        __syncwarp();
-        if (lane == 0) bt[c] = csub(bt[c], f);
-        for (int64_t i = lane; i <= c; i += 32) bb[i] = csub(bb[i], cmul(f, Uu[i + c * Nb]));
+        if constexpr (sizeof(TC) == 4) {
+          // single precision with compensated sums; lane 0 forms
+          // t (u_c^H b + b_c) in FP64 and broadcasts it
+          const float2* Uf = a.fbase + b.rf_off + right * Nb * Nb + c * Nb;
+          KSum<float> ks;
+          for (int64_t i = lane; i <= c; i += 32) {
+            const float2 u = Uf[i], x = bb[i];
+            ks.add(u.x * x.x + u.y * x.y, u.x * x.y - u.y * x.x);
+          }
+          const float2 btc = bt[c];
+          ks.add(lane == 0 ? btc.x : 0.f, lane == 0 ? btc.y : 0.f);
+          const TCx<float> f = warp_ksum_scaled<float>(ks, t);
+          __syncwarp();
+          if (lane == 0) bt[c] = make_float2(btc.x - f.x, btc.y - f.y);
+          for (int64_t i = lane; i <= c; i += 32) {
+            const float2 u = Uf[i], x = bb[i];
+            bb[i] = make_float2(x.x - (f.x * u.x - f.y * u.y), x.y - (f.x * u.y + f.y * u.x));
+          }
+        } else {
+          const double2* Uu = a.zbase + b.rs_off + right * Nb * Nb;
+          double2 s = make_double2(0.0, 0.0);
+          for (int64_t i = lane; i <= c; i += 32) s = cadd(s, cmulc(Uu[i + c * Nb], bb[i]));
+          s = cadd(warp_csum(s), bt[c]);
+          const double2 f = cmul(t, s);
+          __syncwarp();
+          if (lane == 0) bt[c] = csub(bt[c], f);
+          for (int64_t i = lane; i <= c; i += 32) bb[i] = csub(bb[i], cmul(f, Uu[i + c * Nb]));
+        }
         __syncwarp();
       }
     }
@@ -443,41 +676,53 @@ __device__ void leaf_modes_complex(const BatchArgs& a, const BinDesc& b, int64_t
     }
     __syncthreads();
   }
-  // U_leaf = Q_leaf [B; 0]: reflectors in reverse order, a warp per column
+  // U_leaf = Q_leaf [B; 0]: reflectors in reverse order; a warp per mode
+  // column, held in registers; each reflector staged once in shared memory
   const int64_t r0 = bin_leaf_begin(b, leaf), h = bin_leaf_begin(b, leaf + 1) - r0;
   const V* Y = (const V*)a.ybase + b.y_off + r0;
   const double2* tl = a.zbase + b.tau_off + leaf * Nb;
   float2* Uo = b.U + r0;
-  for (int64_t col = warp; col < k; col += nwarps) {
-    for (int64_t i = lane; i < h; i += 32) {
-      const double2 v = (i < Nb) ? Bt[i + col * Nb] : make_double2(0.0, 0.0);
-      Uo[i + col * b.ldu] = make_float2((float)v.x, (float)v.y);
+  constexpr int EL = LeafCap<TC>::EL;
+  for (int64_t c0 = 0; c0 < k; c0 += nwarps) {
+    const int64_t col = c0 + warp;
+    const bool live = col < k;
+    TCx<TC> x[EL];
+#pragma unroll
+    for (int e = 0; e < EL; ++e) {
+      const int64_t i = lane + 32 * e;
+      TB v{};
+      if (live && i < Nb) v = Bt[i + col * Nb];
+      x[e] = {(TC)v.x, (TC)v.y};
     }
-  }
-  __syncthreads();
-  for (int64_t col = warp; col < k; col += nwarps) {
-    float2* u = Uo + col * b.ldu;
     for (int64_t j = Nb - 1; j >= 0; --j) {
       const double2 t = tl[j];
-      if (t.x == 0.0 && t.y == 0.0) continue;
-      const TCx<TC> one = {(TC)1, (TC)0};
+      if (t.x == 0.0 && t.y == 0.0) continue;   // uniform across the block
+      __syncthreads();
+      for (int64_t i = j + tid; i < h; i += blockDim.x)
+        CT<TC>::stt(sv + i, (i == j) ? TCx<TC>{(TC)1, (TC)0} : CT<TC>::ldt(Y + i + j * b.N));
+      __syncthreads();
       KSum<TC> ks;
-      for (int64_t i = j + lane; i < h; i += 32) {
-        const TCx<TC> v = (i == j) ? one : CT<TC>::ldt(Y + i + j * b.N);
-        const float2 x = u[i];
-        const TCx<TC> p = tc_mulc(v, TCx<TC>{(TC)x.x, (TC)x.y});
-        ks.add(p.x, p.y);
+#pragma unroll
+      for (int e = 0; e < EL; ++e) {
+        const int64_t i = lane + 32 * e;
+        if (i >= j && i < h) {
+          const TCx<TC> p = tc_mulc(CT<TC>::ldt(sv + i), x[e]);
+          ks.add(p.x, p.y);
+        }
       }
-      const double2 d = warp_csum(ks.get());
-      const TCx<TC> f = tc_of<TC>(cmul(t, d));
-      __syncwarp();
-      for (int64_t i = j + lane; i < h; i += 32) {
-        const TCx<TC> v = (i == j) ? one : CT<TC>::ldt(Y + i + j * b.N);
-        const float2 x = u[i];
-        const TCx<TC> nv = tc_sub(TCx<TC>{(TC)x.x, (TC)x.y}, tc_mul(f, v));
-        u[i] = make_float2((float)nv.x, (float)nv.y);
+      const TCx<TC> f = warp_ksum_scaled<TC>(ks, t);
+#pragma unroll
+      for (int e = 0; e < EL; ++e) {
+        const int64_t i = lane + 32 * e;
+        if (i >= j && i < h) x[e] = tc_sub(x[e], tc_mul(f, CT<TC>::ldt(sv + i)));
       }
-      __syncwarp();
+    }
+    if (live) {
+#pragma unroll
+      for (int e = 0; e < EL; ++e) {
+        const int64_t i = lane + 32 * e;
+        if (i < h) Uo[i + col * b.ldu] = make_float2((float)x[e].x, (float)x[e].y);
+      }
     }
   }
 }
@@ -491,6 +736,12 @@ __global__ void __launch_bounds__(kBThreads) svd_batched_kernel(BatchArgs a) {
   __shared__ double2 sred[kBThreads / 32];
   __shared__ int si[4 + kMaxNb];
   __shared__ int s_item, s_prev;
+  // the current reflector of a leaf (at most 1024 complex64 or 512 complex128 rows)
+  __shared__ __align__(16) unsigned char svraw[8192];
+  __shared__ double2 smerge[kMergeSmem];
+  using V = typename CT<TC>::V;
+  V* sv = (V*)svraw;
+  static_assert(kLeafMaxRowsF * 8 <= 8192 && kLeafMaxRowsD * 16 <= 8192, "reflector stage too small");
   const int tid = threadIdx.x;
   double2* scratch = a.scratch + (int64_t)blockIdx.x * 2 * kMaxNb * kMaxK;
   // phase A
@@ -504,7 +755,7 @@ __global__ void __launch_bounds__(kBThreads) svd_batched_kernel(BatchArgs a) {
     const int f = a.itemsA[item].x;
     const int64_t leaf = a.itemsA[item].y;
     const BinDesc b = a.bins[f];
-    leaf_qr_complex<TC>(a, b, leaf, sd, sred);
+    leaf_qr_complex<TC>(a, b, leaf, sd, sred, sv);
     __threadfence();
     __syncthreads();
     int64_t node = leaf;
@@ -525,7 +776,8 @@ __global__ void __launch_bounds__(kBThreads) svd_batched_kernel(BatchArgs a) {
       if (prev == 0) { root = false; break; }
       __threadfence();
       tree_merge_complex(a.zbase + b.rs_off + left * b.Nb * b.Nb, a.zbase + b.rs_off + right * b.Nb * b.Nb,
-                         a.zbase + b.taut_off + right * b.Nb, b.Nb, sd);
+                         a.zbase + b.taut_off + right * b.Nb, b.Nb, sd,
+                         sizeof(TC) == 4 ? a.fbase + b.rf_off + right * b.Nb * b.Nb : nullptr, smerge);
       __threadfence();
       __syncthreads();
       node = left;
@@ -575,7 +827,7 @@ __global__ void __launch_bounds__(kBThreads) svd_batched_kernel(BatchArgs a) {
     const int f = __ldcg(&a.ready[item].x);
     const int64_t leaf = __ldcg(&a.ready[item].y);
     const BinDesc b = a.bins[f];
-    leaf_modes_complex<TC>(a, b, leaf, scratch);
+    leaf_modes_complex<TC>(a, b, leaf, scratch, sv);
     __syncthreads();
   }
 }
@@ -596,6 +848,7 @@ struct pylom_batched_plan {
   std::vector<pylom::BinDesc> bins;   // offsets filled by the plan, pointers by bind
   std::vector<int2> itemsA;
   int nA = 0, nD = 0;
+  size_t off_f = 0;   // complex64 node-reflector copies
   size_t off_cnt = 0, off_bins = 0, off_items = 0, off_ready = 0, off_u = 0, off_z = 0, off_y = 0,
          off_scr = 0, bytes = 0;
   int64_t total_u = 0, total_z = 0, total_y = 0, total_s = 0;
@@ -608,10 +861,11 @@ namespace pylom {
 constexpr int64_t kBatchedMaxNb = kMaxNb;
 constexpr int64_t kBatchedMaxK = kMaxK;
 
+// Longest leaf a bin may have: a warp holds a leaf column in registers.
+int64_t batched_max_leaf_rows(int prec) { return prec == PYLOM_PREC_FP64 ? kLeafMaxRowsD : kLeafMaxRowsF; }
+
 int64_t batched_default_leaf_rows(int64_t N, int64_t Nb, int prec) {
-  // about 1 MiB of working copy per leaf (L2-friendly with ~300 leaves in flight)
-  const int64_t elem = (prec == PYLOM_PREC_FP64) ? 16 : 8;
-  int64_t h = (int64_t)(1 << 20) / (Nb * elem);
+  int64_t h = batched_max_leaf_rows(prec);
   if (h < Nb) h = Nb;
   if (h > N) h = N;
   return h;
@@ -655,7 +909,7 @@ extern "C" pylom_status pylom_svd_batched_plan(int nbins, const int64_t* N, cons
   p->prec = prec;
   p->kmodes = kmodes;
   const size_t ye = (prec == PYLOM_PREC_FP64) ? 16 : 8;
-  int64_t y = 0, z = 0, u = 0, sacc = 0;
+  int64_t y = 0, z = 0, u = 0, sacc = 0, fz = 0;
   for (int f = 0; f < nbins; ++f) {
     const int64_t n = N[f], nb = Nb[f];
     if (nb < 1 || nb > kBatchedMaxNb || n < nb) {
@@ -671,6 +925,11 @@ extern "C" pylom_status pylom_svd_batched_plan(int nbins, const int64_t* N, cons
       return PYLOM_ERR_SHAPE;
     }
     int64_t P = n / h;
+    // no leaf longer than the register-resident limit (with the floor
+    // partition the longest leaf has ceil(n / P) rows; the shortest keeps
+    // >= Nb rows because the limit is at least 2 Nb)
+    const int64_t hmax = batched_max_leaf_rows(prec);
+    if (P < (n + hmax - 1) / hmax) P = (n + hmax - 1) / hmax;
     if (P < 1) P = 1;
     const int64_t np = nb + (nb & 1);
     BinDesc b{};
@@ -681,6 +940,7 @@ extern "C" pylom_status pylom_svd_batched_plan(int nbins, const int64_t* N, cons
     b.taut_off = z;              z += P * nb;
     b.jac_off = z;               z += 2 * np * np;
     b.ur_off = z;                z += nb * nb;
+    b.rf_off = fz;               fz += (prec == PYLOM_PREC_FP64) ? 0 : P * nb * nb;
     b.arr_off = u;               u += P;
     b.s_off = sacc;              sacc += nb;
     p->N.push_back(n); p->Nb.push_back(nb); p->P.push_back(P); p->h.push_back(h);
@@ -710,6 +970,7 @@ extern "C" pylom_status pylom_svd_batched_plan(int nbins, const int64_t* N, cons
   p->off_ready = off; off += align256(sizeof(int3) * (size_t)(p->nD > 0 ? p->nD : 1));
   p->off_u = off;     off += align256(sizeof(unsigned) * (size_t)u);
   p->off_z = off;     off += align256(sizeof(double2) * (size_t)z);
+  p->off_f = off;     off += align256(sizeof(float2) * (size_t)(fz > 0 ? fz : 1));
   p->off_y = off;     off += align256(ye * (size_t)y);
   p->off_scr = off;   off += align256(sizeof(double2) * (size_t)p->grid * 2 * kMaxNb * kMaxK);
   p->bytes = off;
@@ -811,6 +1072,7 @@ extern "C" pylom_status pylom_svd_batched_run(const pylom_batched_plan* plan, vo
   a.nD = plan->nD;
   a.ybase = base + plan->off_y;
   a.zbase = (double2*)(base + plan->off_z);
+  a.fbase = (float2*)(base + plan->off_f);
   a.ubase = (unsigned*)(base + plan->off_u);
   a.S = S;
   a.scratch = (double2*)(base + plan->off_scr);

@@ -47,7 +47,8 @@ def _save(d):
 
 
 def candidates(N: int, Nb: int):
-    c = sorted({max(Nb, h) for h in (256, 512, 1024, 2048, 4096, 8192, 16384)})
+    # the library splits leaves longer than 1024 rows (512 for complex128)
+    c = sorted({max(Nb, h) for h in (256, 384, 512, 768, 1024)})
     return [h for h in c if h <= N]
 
 
