@@ -140,6 +140,28 @@ __device__ __forceinline__ TCx<double> warp_ksum_scaled<double>(const KSum<doubl
   return {f.x, f.y};
 }
 
+// Warp total of the real part of a compensated sum as (sum, compensation),
+// valid in lane 0.
+template <typename TC>
+__device__ __forceinline__ double2 warp_ksum_pair(const KSum<TC>& k) {
+  if constexpr (sizeof(TC) == 4) {
+    float s = (float)k.sx, c = -(float)k.cx;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float os = __shfl_xor_sync(0xffffffffu, s, o), oc = __shfl_xor_sync(0xffffffffu, c, o);
+      two_sum_f(s, c, os, oc);
+    }
+    double2 r = make_double2(0.0, 0.0);
+    if ((threadIdx.x & 31) == 0) r = make_double2((double)s, (double)c);
+    return r;
+  } else {
+    double v = (double)k.sx - (double)k.cx;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return make_double2(v, 0.0);
+  }
+}
+
 // Block total of the real part of a compensated sum, valid in thread 0
 // (scratch: one double2 per warp).
 template <typename TC>
@@ -261,16 +283,31 @@ __device__ void leaf_qr_complex(const BatchArgs& a, const BinDesc& b, int64_t le
     }
   if (bad) raise_status(a.hdr, PYLOM_ERR_NONFINITE);
   __syncthreads();
+  // sd[3]: squared norm below the diagonal of the next column, left there by
+  // the warp that updated that column (x = sum + compensation); sd[4].x = 1
+  // when it is valid
+  if (tid == 0) sd[4] = make_double2(0.0, 0.0);
+  __syncthreads();
   for (int64_t j = 0; j < Nb; ++j) {
-    // squared norm below the diagonal of column j
-    KSum<TC> ks;
-    for (int64_t i = j + 1 + tid; i < h; i += nthr) {
-      const TCx<TC> y = CT<TC>::ldt(Y + i + j * ldy);
-      ks.add(y.x * y.x + y.y * y.y, (TC)0);
+    double xx0 = 0.0;
+    // every thread reads the flag before thread 0 resets it below, so the
+    // branch (which holds block barriers) is taken by all threads alike
+    const bool have_norm = sd[4].x != 0.0;
+    __syncthreads();
+    if (!have_norm) {
+      // squared norm below the diagonal of column j, by a block pass
+      KSum<TC> ks;
+      for (int64_t i = j + 1 + tid; i < h; i += nthr) {
+        const TCx<TC> y = CT<TC>::ldt(Y + i + j * ldy);
+        ks.add(y.x * y.x + y.y * y.y, (TC)0);
+      }
+      xx0 = block_real_sum0<TC>(ks, sred);
+    } else if (tid == 0) {
+      xx0 = sd[3].x + sd[3].y;
     }
     // thread 0 forms the reflector's scalars and broadcasts them
-    const double xx0 = block_real_sum0<TC>(ks, sred);
     if (tid == 0) {
+      sd[4] = make_double2(0.0, 0.0);
       const double2 alpha = CT<TC>::ld(Y + j + j * ldy);
       double2 t0 = make_double2(0.0, 0.0), scale0 = make_double2(0.0, 0.0);
       double beta0 = alpha.x;
@@ -328,6 +365,22 @@ __device__ void leaf_qr_complex(const BatchArgs& a, const BinDesc& b, int64_t le
         for (int e = 0; e < EL; ++e) {
           const int64_t i = j + lane + 32 * e;
           if (i < h) CT<TC>::stt(yc + i, tc_sub(x[e], tc_mul(f, CT<TC>::ldt(sv + i))));
+        }
+        if (c == j + 1) {
+          // the next column's squared norm below its diagonal, re-read by the
+          // lanes that just wrote it
+          __syncwarp();
+          KSum<TC> kn;
+          for (int64_t i = j + lane; i < h; i += 32) {   // the rows this lane stored
+            if (i <= j + 1) continue;
+            const TCx<TC> y = CT<TC>::ldt(yc + i);
+            kn.add(y.x * y.x + y.y * y.y, (TC)0);
+          }
+          const double2 nn = warp_ksum_pair<TC>(kn);
+          if (lane == 0) {
+            sd[3] = nn;
+            sd[4] = make_double2(1.0, 0.0);
+          }
         }
       }
     }
@@ -528,12 +581,28 @@ __device__ void bin_jacobi(const BatchArgs& a, const BinDesc& b, double2* sd, in
         al = warp_sum(al);
         be = warp_sum(be);
         ga = warp_csum(ga);
-        const double g = sqrt(cabs2(ga));
-        if (g != 0.0 && g > tol * sqrt(al * be)) {
-          const double2 eph = cscale(cconj(ga), 1.0 / g);   // e^{-i phi}
-          const double zeta = (be - al) / (2.0 * g);
-          const double t = ((zeta >= 0.0) ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        // every lane holds the same sums; lane 0 alone forms the rotation
+        // (FP64 square roots and divisions are slow on this part)
+        int rot = 0;
+        double c = 0.0, s = 0.0;
+        double2 eph = make_double2(0.0, 0.0);   // e^{-i phi}
+        if (lane == 0) {
+          const double g = sqrt(cabs2(ga));
+          if (g != 0.0 && g > tol * sqrt(al * be)) {
+            eph = cscale(cconj(ga), 1.0 / g);
+            const double zeta = (be - al) / (2.0 * g);
+            const double t = ((zeta >= 0.0) ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = c * t;
+            rot = 1;
+          }
+        }
+        rot = __shfl_sync(0xffffffffu, rot, 0);
+        if (rot) {
+          c = __shfl_sync(0xffffffffu, c, 0);
+          s = __shfl_sync(0xffffffffu, s, 0);
+          eph.x = __shfl_sync(0xffffffffu, eph.x, 0);
+          eph.y = __shfl_sync(0xffffffffu, eph.y, 0);
           for (int64_t r = lane; r < Nb; r += 32) {
             const double2 x = A[r + i * Nb], y = cmul(eph, A[r + j * Nb]);
             A[r + i * Nb] = csub(cscale(x, c), cscale(y, s));
@@ -731,7 +800,7 @@ __device__ void leaf_modes_complex(const BatchArgs& a, const BinDesc& b, int64_t
 // the persistent kernel
 // ---------------------------------------------------------------------------
 template <typename TC>
-__global__ void __launch_bounds__(kBThreads) svd_batched_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(kBThreads, 2) svd_batched_kernel(BatchArgs a) {
   __shared__ double2 sd[8 + kMaxNb / 2 + 4];
   __shared__ double2 sred[kBThreads / 32];
   __shared__ int si[4 + kMaxNb];
