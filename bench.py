@@ -112,7 +112,10 @@ def cpu_baseline(n_rows: int, M: int, seed_shift: int = 0):
 
 def bench_adjoint(args, dev):
     """Forward + hand-written backward of the truncated-POD reconstruction
-    loss on the 4,194,304 x 256 float32 known-spectrum matrix, r = 20."""
+    loss on the 4,194,304 x 256 float32 known-spectrum matrix, r = 20: timed
+    on the mixed-precision path (FP32 modes, 3xTF32 products on tcgen05,
+    binary64 tree passes and square SVD adjoint) and, for comparison, on the
+    binary64 path."""
     import torch
     import paper_2405_15529_gb300 as pg
     import synth
@@ -122,33 +125,45 @@ def bench_adjoint(args, dev):
 
     def loss(Xg, U):
         Yw = Xg.double() * torch.sqrt(w)[:, None]
-        return torch.sum((Yw - U @ (U.T @ Yw)) ** 2)
+        Ud = U.double()
+        return torch.sum((Yw - Ud @ (Ud.T @ Yw)) ** 2)
 
-    def step():
-        Xg = X.detach().requires_grad_(True)
-        U, S, VT = pg.pod_autograd(Xg, r, w=w)
-        loss(Xg, U).backward()
-        return Xg.grad, U
+    def run(prec, steps, warmup):
+        def step():
+            Xg = X.detach().requires_grad_(True)
+            U, S, VT = pg.pod_autograd(Xg, r, w=w, prec=prec)
+            loss(Xg, U).backward()
+            return Xg.grad, U
 
-    for _ in range(max(1, args.warmup - 2)):
-        step()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.adj_steps):
-        G, U = step()
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.adj_steps
-    with torch.no_grad():
-        Yw = X.double() * torch.sqrt(w)[:, None]
-        Gc = 2.0 * torch.sqrt(w)[:, None] * (Yw - U @ (U.T @ Yw))
-        rel = (torch.linalg.norm(G.double() - Gc) / torch.linalg.norm(Gc)).item()
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            G, U = step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        with torch.no_grad():
+            Ud = U.double()
+            Yw = X.double() * torch.sqrt(w)[:, None]
+            Gc = 2.0 * torch.sqrt(w)[:, None] * (Yw - Ud @ (Ud.T @ Yw))
+            rel = (torch.linalg.norm(G.double() - Gc) / torch.linalg.norm(Gc)).item()
+        del G, U, Ud, Yw, Gc
+        torch.cuda.empty_cache()
+        return ms, rel
+
+    ms, rel = run(pg.PREC_MIXED_3XTF32, args.adj_steps, max(1, args.warmup - 2))
+    ms64, rel64 = run(pg.PREC_FP64, 1, 1)
     out = {"workload": "known_spectrum_4194304x256_f32_weighted_r20_loss_grad", "ms_per_step": ms,
            "value": N * M * 4 / (ms * 1e-3) / 1e9, "unit": "GB/s of X (forward + backward)",
-           "steps": args.adj_steps, "grad_rel_err_vs_closed_form": rel,
+           "steps": args.adj_steps, "precision": "mixed (3xTF32 tcgen05; binary64 tree and square SVD adjoint)",
+           "grad_rel_err_vs_closed_form": rel,
+           "fp64_path_ms_same_x": ms64, "fp64_path_grad_rel_err_vs_closed_form": rel64,
+           "speedup_vs_fp64_path": ms64 / ms,
            "note": "step = pylom_pod forward (check) + torch loss + pylom_pod_backward"}
-    del X, XT, w, G, U, Yw, Gc
+    del X, XT, w
     torch.cuda.empty_cache()
     return out
 

@@ -147,9 +147,14 @@ pylom_status pylom_pod(const void* X, int64_t N, int64_t M, int64_t ldx, int xty
  * tree reflectors that the forward call left in its workspace (Q^T dU by
  * the leaf reflectors and a bottom-up tree pass; Q [B; 0] by the top-down
  * pass); the square SVD adjoint of R runs in binary64 on M x M matrices.
- *  fwd_ws, fwd_ws_bytes  the workspace of the PYLOM_PREC_FP64 pylom_pod
- *                        call being differentiated, unchanged since (same
- *                        N, M, leaf_rows, r_max, w, remove_mean, mode_kind).
+ *  fwd_ws, fwd_ws_bytes  the workspace of the pylom_pod call being
+ *                        differentiated, unchanged since (same N, M,
+ *                        leaf_rows, r_max, w, remove_mean, mode_kind, prec).
+ *  prec    that call's precision: PYLOM_PREC_FP64 (Q applied in binary64 on
+ *          the FP64 tensor pipe) or PYLOM_PREC_MIXED_3XTF32 (Q^T dU and
+ *          Q [B; 0] by the forward's FP32 reflectors in 3xTF32 on tcgen05,
+ *          dU C in FP32; the tree passes and the square SVD adjoint stay
+ *          binary64).
  *  r       number of modes whose cotangent dU holds (0 <= r <= r_max).
  *  S, VT   that call's singular values and right vectors (ldvt >= M).
  *  dU      N x r (lddu >= N) or NULL; dS: M or NULL; dVT: M x M or NULL.
@@ -158,10 +163,10 @@ pylom_status pylom_pod(const void* X, int64_t N, int64_t M, int64_t ldx, int xty
  * singular values of the r modes that carry a cotangent must be nonzero
  * (R itself may be singular, as it is once the mean is removed).
  * ------------------------------------------------------------------------ */
-size_t pylom_pod_backward_workspace_size(int64_t N, int64_t M, int64_t leaf_rows, int64_t r);
+size_t pylom_pod_backward_workspace_size(int64_t N, int64_t M, int64_t leaf_rows, int64_t r, int prec);
 pylom_status pylom_pod_backward(const void* fwd_ws, size_t fwd_ws_bytes, int64_t N, int64_t M,
                                 int64_t leaf_rows, int64_t r_max, int64_t r, const double* w,
-                                int remove_mean, int mode_kind, const double* S, const double* VT,
+                                int remove_mean, int mode_kind, int prec, const double* S, const double* VT,
                                 int64_t ldvt, const double* dU, int64_t lddu, const double* dS,
                                 const double* dVT, int64_t lddvt, void* dX, int64_t lddx, int dxtype,
                                 void* ws, size_t ws_bytes, void* stream);

@@ -94,9 +94,9 @@ def load_library(path: str = LIB_PATH):
     lib.pylom_profile_end.restype = _int
     lib.pylom_profile_end.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_int)]
     lib.pylom_pod_backward_workspace_size.restype = _sz
-    lib.pylom_pod_backward_workspace_size.argtypes = [_i64, _i64, _i64, _i64]
+    lib.pylom_pod_backward_workspace_size.argtypes = [_i64, _i64, _i64, _i64, _int]
     lib.pylom_pod_backward.restype = _int
-    lib.pylom_pod_backward.argtypes = [_vp, _sz, _i64, _i64, _i64, _i64, _i64, _vp, _int, _int, _vp, _vp,
+    lib.pylom_pod_backward.argtypes = [_vp, _sz, _i64, _i64, _i64, _i64, _i64, _vp, _int, _int, _int, _vp, _vp,
                                        _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, _int, _vp, _sz, _vp]
     lib.pylom_svd_batched_plan.restype = _int
     lib.pylom_svd_batched_plan.argtypes = [_int, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
@@ -210,6 +210,7 @@ class PodResult:
     r: int
     sweeps: int
     workspace: "torch.Tensor"
+    prec: int = 0            # PREC_FP64 or PREC_MIXED_3XTF32 (the backward needs it)
 
 
 def pod_workspace_size(N, M, leaf_rows=0, r_max=None, xtype=F64, prec=PREC_FP64) -> int:
@@ -260,7 +261,7 @@ def pod(X, w=None, remove_mean=True, energy=0.0, r_max=None, mode_kind=MODES_ORT
         st, r, sweeps = workspace_status(workspace, stream)
         _raise(st, "pylom_pod (device)")
         U = U[:, :r]
-    return PodResult(U=U, S=S, VT=VT, mean=mean, r=r, sweeps=sweeps, workspace=workspace)
+    return PodResult(U=U, S=S, VT=VT, mean=mean, r=r, sweeps=sweeps, workspace=workspace, prec=int(prec))
 
 
 def tsqr(A, leaf_rows=0, want_q=True, prec=PREC_FP64, stream=None, check=True):
@@ -371,13 +372,14 @@ def pod_backward(fwd: PodResult, X_shape, w, remove_mean, mode_kind, leaf_rows, 
         dVT = _colmajor(dVT.to(torch.float64))
     if w is not None:
         w = w.to(device=dev, dtype=torch.float64).contiguous()
-    need = lib.pylom_pod_backward_workspace_size(N, M, leaf_rows, r)
+    need = lib.pylom_pod_backward_workspace_size(N, M, leaf_rows, r, int(fwd.prec))
     if need == 0:
         _raise(ERR_SHAPE, "pylom_pod_backward_workspace_size")
     ws = torch.empty(need, dtype=torch.uint8, device=dev)
     dX = empty_colmajor(N, M, dx_dtype, dev)
     st = lib.pylom_pod_backward(_dptr(fwd.workspace), fwd.workspace.numel(), N, M, leaf_rows, r_max, r,
-                                _dptr(w), int(bool(remove_mean)), int(mode_kind), _dptr(fwd.S), _dptr(fwd.VT),
+                                _dptr(w), int(bool(remove_mean)), int(mode_kind), int(fwd.prec), _dptr(fwd.S),
+                                _dptr(fwd.VT),
                                 _ld(fwd.VT), _dptr(dU), _ld(dU) if dU is not None else N, _dptr(dS),
                                 _dptr(dVT), _ld(dVT) if dVT is not None else M, _dptr(dX), _ld(dX), dxt,
                                 _dptr(ws), ws.numel(), _stream(stream))
@@ -397,9 +399,9 @@ def _make_pod_function():
         hand-written TSQR + small-SVD adjoint.  Returns (U_r, S, VT)."""
 
         @staticmethod
-        def forward(ctx, X, w, r, remove_mean, mode_kind, leaf_rows):
+        def forward(ctx, X, w, r, remove_mean, mode_kind, leaf_rows, prec):
             res = pod(X.detach(), w=w, remove_mean=remove_mean, energy=0.0, r_max=r, mode_kind=mode_kind,
-                      leaf_rows=leaf_rows, check=True)
+                      leaf_rows=leaf_rows, prec=prec, check=True)
             ctx.fwd = res
             ctx.meta = (tuple(X.shape), X.dtype, w, remove_mean, mode_kind, leaf_rows, r)
             return res.U.clone(), res.S.clone(), res.VT.clone()
@@ -409,7 +411,7 @@ def _make_pod_function():
             shape, dtype, w, remove_mean, mode_kind, leaf_rows, r = ctx.meta
             dX = pod_backward(ctx.fwd, shape, w, remove_mean, mode_kind, leaf_rows, r, dU=gU, dS=gS, dVT=gVT,
                               dx_dtype=dtype)
-            return dX, None, None, None, None, None
+            return dX, None, None, None, None, None, None
 
     return PodFn
 
@@ -417,12 +419,13 @@ def _make_pod_function():
 _PodFn = None
 
 
-def pod_autograd(X, r, w=None, remove_mean=False, mode_kind=MODES_ORTHONORMAL, leaf_rows=0):
-    """Differentiable POD: (U_r, S, VT) with the hand-written adjoint."""
+def pod_autograd(X, r, w=None, remove_mean=False, mode_kind=MODES_ORTHONORMAL, leaf_rows=0, prec=PREC_FP64):
+    """Differentiable POD: (U_r, S, VT) with the hand-written adjoint (prec:
+    PREC_FP64, or PREC_MIXED_3XTF32 for FP32 modes and a tcgen05 adjoint)."""
     global _PodFn
     if _PodFn is None:
         _PodFn = _make_pod_function()
-    return _PodFn.apply(X, w, int(r), bool(remove_mean), int(mode_kind), int(leaf_rows))
+    return _PodFn.apply(X, w, int(r), bool(remove_mean), int(mode_kind), int(leaf_rows), int(prec))
 
 
 class BatchedSVD:

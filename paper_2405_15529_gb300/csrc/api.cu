@@ -230,14 +230,15 @@ extern "C" pylom_status pylom_profile_end(double* phase_ms, int* calls) {
 // adjoint of the POD path
 // ---------------------------------------------------------------------------
 
-extern "C" size_t pylom_pod_backward_workspace_size(int64_t N, int64_t M, int64_t leaf_rows, int64_t r) {
+extern "C" size_t pylom_pod_backward_workspace_size(int64_t N, int64_t M, int64_t leaf_rows, int64_t r, int prec) {
   if (!tall_shape_ok(N, M, leaf_rows) || r < 0 || r > M) return 0;
-  return pod_backward_bytes(N, M, leaves_of(N, M, leaf_rows), r);
+  if (prec != PYLOM_PREC_FP64 && prec != PYLOM_PREC_MIXED_3XTF32) return 0;
+  return pod_backward_bytes(N, M, leaves_of(N, M, leaf_rows, prec), r);
 }
 
 extern "C" pylom_status pylom_pod_backward(const void* fwd_ws, size_t fwd_ws_bytes, int64_t N, int64_t M,
                                            int64_t leaf_rows, int64_t r_max, int64_t r, const double* w,
-                                           int remove_mean, int mode_kind, const double* S,
+                                           int remove_mean, int mode_kind, int prec, const double* S,
                                            const double* VT, int64_t ldvt, const double* dU,
                                            int64_t lddu, const double* dS, const double* dVT,
                                            int64_t lddvt, void* dX, int64_t lddx, int dxtype,
@@ -248,6 +249,9 @@ extern "C" pylom_status pylom_pod_backward(const void* fwd_ws, size_t fwd_ws_byt
     return fail(PYLOM_ERR_ARG, "pylom_pod_backward: dxtype must be PYLOM_F32 or PYLOM_F64");
   if (mode_kind != PYLOM_MODES_ORTHONORMAL && mode_kind != PYLOM_MODES_PHYSICAL)
     return fail(PYLOM_ERR_ARG, "pylom_pod_backward: bad mode_kind %d", mode_kind);
+  if (prec != PYLOM_PREC_FP64 && prec != PYLOM_PREC_MIXED_3XTF32)
+    return fail(PYLOM_ERR_ARG, "pylom_pod_backward: bad prec %d", prec);
+  const bool mixed = prec == PYLOM_PREC_MIXED_3XTF32;
   if (leaf_rows < 0 || !tall_shape_ok(N, M, leaf_rows))
     return fail(PYLOM_ERR_SHAPE, "pylom_pod_backward: bad shape (N=%lld M=%lld b=%lld)", (long long)N,
                 (long long)M, (long long)leaf_rows);
@@ -255,8 +259,8 @@ extern "C" pylom_status pylom_pod_backward(const void* fwd_ws, size_t fwd_ws_byt
     return fail(PYLOM_ERR_SHAPE, "pylom_pod_backward: need 1 <= r_max <= M and 0 <= r <= r_max");
   if (ldvt < M || (dU && lddu < N) || (dVT && lddvt < M) || lddx < N)
     return fail(PYLOM_ERR_ARG, "pylom_pod_backward: leading dimension too small");
-  const int64_t P = leaves_of(N, M, leaf_rows);
-  if (!aligned256(fwd_ws) || fwd_ws_bytes < pod_bytes(N, M, P, r_max))
+  const int64_t P = leaves_of(N, M, leaf_rows, prec);
+  if (!aligned256(fwd_ws) || fwd_ws_bytes < pod_bytes(N, M, P, r_max, prec))
     return fail(PYLOM_ERR_WORKSPACE, "pylom_pod_backward: forward workspace does not match N, M, b, r_max");
   const size_t need = pod_backward_bytes(N, M, P, r);
   if (!aligned256(ws) || ws_bytes < need)
@@ -265,13 +269,14 @@ extern "C" pylom_status pylom_pod_backward(const void* fwd_ws, size_t fwd_ws_byt
   char* fbase = (char*)fwd_ws;
   TsqrState fs;
   fs.hdr = (WsHeader*)fbase;
-  tsqr_state_carve(fs, fbase + sizeof(WsHeader), N, M, P, r_max);
-  const double* UR =
-      (const double*)(fbase + sizeof(WsHeader) + tsqr_state_bytes(N, M, P, r_max) + svd_state_bytes(M));
+  tsqr_state_carve(fs, fbase + sizeof(WsHeader), N, M, P, r_max, !mixed);
+  char* p2 = fbase + sizeof(WsHeader) + tsqr_state_bytes(N, M, P, r_max, !mixed);
+  const double* UR = (const double*)(p2 + svd_state_bytes(M));
+  char* extra = mixed ? p2 + svd_state_bytes(M) + align256(sizeof(double) * (size_t)M * M) : nullptr;
   cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(WsHeader), st);
   if (e != cudaSuccess) return cuda_fail(e, "pylom_pod_backward: header clear");
   e = launch_pod_backward(fs, UR, S, VT, ldvt, dU, lddu, dS, dVT, lddvt, w, remove_mean,
-                          mode_kind == PYLOM_MODES_PHYSICAL, r, dX, lddx, dxtype, (char*)ws, st);
+                          mode_kind == PYLOM_MODES_PHYSICAL, r, dX, lddx, dxtype, (char*)ws, extra, st);
   if (e != cudaSuccess) return cuda_fail(e, "pylom_pod_backward");
   return PYLOM_OK;
 }

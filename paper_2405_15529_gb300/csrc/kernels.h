@@ -93,7 +93,10 @@ cudaError_t launch_pod_backward(const TsqrState& fs, const double* UR, const dou
                                 int64_t ldvt, const double* dU, int64_t lddu, const double* dS,
                                 const double* dVT, int64_t lddvt, const double* w, int remove_mean,
                                 int physical, int64_t r, void* dX, int64_t lddx, int dxtype,
-                                char* bw_base, cudaStream_t st);
+                                char* bw_base, char* mixed_extra, cudaStream_t st);
+// Mixed-precision adjoint support (tsqr_mixed.cu): per leaf C := Q_leaf^T C
+// (FP32, ld N) on tcgen05, top M rows into the binary64 slots Z.
+cudaError_t launch_leaf_qt_mixed(const TsqrState& s, char* extra, float* C, int64_t r, double* Z, cudaStream_t st);
 
 // Records a message for pylom_last_error() on the calling host thread.
 void set_error_message(const char* fmt, ...);

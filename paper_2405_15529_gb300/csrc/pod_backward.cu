@@ -175,8 +175,8 @@ __global__ void __launch_bounds__(256) bw_add_du_c_kernel(const double* dU, cons
 }
 
 // dX = W^(1/2) dY, then minus each row's mean (adjoint of mean removal).
-template <typename TX>
-__global__ void bw_finalize_kernel(const double* dY, const double* w, int remove_mean, TX* dX,
+template <typename TX, typename TY>
+__global__ void bw_finalize_kernel(const TY* dY, const double* w, int remove_mean, TX* dX,
                                    int64_t lddx, int64_t N, int64_t M) {
   for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N;
        n += (int64_t)gridDim.x * blockDim.x) {
@@ -184,10 +184,46 @@ __global__ void bw_finalize_kernel(const double* dY, const double* w, int remove
     double mu = 0.0;
     if (remove_mean) {
       double sum = 0.0;
-      for (int64_t m = 0; m < M; ++m) sum += sw * dY[n + m * N];
+      for (int64_t m = 0; m < M; ++m) sum += sw * (double)dY[n + m * N];
       mu = sum / (double)M;
     }
-    for (int64_t m = 0; m < M; ++m) dX[n + m * lddx] = (TX)(sw * dY[n + m * N] - mu);
+    for (int64_t m = 0; m < M; ++m) dX[n + m * lddx] = (TX)(sw * (double)dY[n + m * N] - mu);
+  }
+}
+
+// Mixed path: dU (N x r, binary64) -> C (FP32, ld N), W^(-1/2) for physical modes.
+__global__ void bw_load_du_f32_kernel(const double* dU, int64_t lddu, const double* w, int physical, float* C,
+                                      int64_t N, int64_t r) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N * r; idx += stride) {
+    const int64_t n = idx % N, c = idx / N;
+    double v = dU[n + c * lddu];
+    if (physical && w) v /= sqrt(w[n]);
+    C[idx] = (float)v;
+  }
+}
+
+// Mixed path: dY (FP32, N x M) += C (N x r) Cm (r x M, binary64, ld r) in
+// FP32; Cm staged per block in shared memory (r <= M <= 4096 columns are
+// taken 64 at a time).
+__global__ void __launch_bounds__(256) bw_add_du_c_f32_kernel(const float* C, const double* Cm, int64_t ldcm,
+                                                              float* dY, int64_t N, int64_t M, int64_t r) {
+  extern __shared__ float scm[];   // r x 64
+  for (int64_t m0 = 0; m0 < M; m0 += 64) {
+    const int64_t mw = (M - m0) < 64 ? (M - m0) : 64;
+    __syncthreads();
+    for (int64_t idx = threadIdx.x; idx < r * mw; idx += blockDim.x) {
+      const int64_t c = idx % r, m = idx / r;
+      scm[c + m * r] = (float)Cm[c + (m0 + m) * ldcm];
+    }
+    __syncthreads();
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+      for (int64_t m = 0; m < mw; ++m) {
+        float acc = 0.f;
+        for (int64_t c = 0; c < r; ++c) acc = fmaf(C[n + c * N], scm[c + m * r], acc);
+        dY[n + (m0 + m) * N] += acc;
+      }
+    }
   }
 }
 
@@ -243,12 +279,25 @@ cudaError_t launch_pod_backward(const TsqrState& fs, const double* UR, const dou
                                 int64_t ldvt, const double* dU, int64_t lddu, const double* dS,
                                 const double* dVT, int64_t lddvt, const double* w, int remove_mean,
                                 int physical, int64_t r, void* dX, int64_t lddx, int dxtype,
-                                char* bw_base, cudaStream_t st) {
+                                char* bw_base, char* mixed_extra, cudaStream_t st) {
   const int64_t N = fs.N, M = fs.M, P = fs.P;
   BwLayout L = carve_backward(bw_base, N, M, P, r);
+  const bool mixed = mixed_extra != nullptr;   // FP32 reflectors of a mixed-precision forward
+  float* C32 = (float*)L.C;
+  float* dY32 = (float*)L.dY;
   cudaError_t e;
   // 1. Z = Q^T dU
-  if (dU && r > 0) {
+  if (mixed && dU && r > 0) {
+    bw_load_du_f32_kernel<<<1024, 256, 0, st>>>(dU, lddu, w, physical, C32, N, r);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_leaf_qt_mixed(fs, mixed_extra, C32, r, L.Z, st)) != cudaSuccess) return e;
+    for (int64_t step = 1; step < P; step <<= 1) {
+      const int64_t merges = (P - step + 2 * step - 1) / (2 * step);
+      dim3 grid((unsigned)merges, (unsigned)((r + 7) / 8));
+      bw_up_pass_kernel<<<grid, 256, 0, st>>>(fs, L.Z, r, step);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+  } else if (dU && r > 0) {
     bw_load_du_kernel<<<1024, 256, 0, st>>>(dU, lddu, w, physical, L.C, N, r);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     static bool attr = false;
@@ -294,6 +343,21 @@ cudaError_t launch_pod_backward(const TsqrState& fs, const double* UR, const dou
   TsqrState ds = fs;
   ds.B = L.B;
   ds.rmax = M;
+  if (mixed) {
+    e = launch_modes_mixed(ds, mixed_extra, L.Bm, M, M, nullptr, 0, dY32, N, nullptr, st, nullptr);
+    if (e != cudaSuccess) return e;
+    if (dU && r > 0) {
+      bw_load_du_f32_kernel<<<1024, 256, 0, st>>>(dU, lddu, w, physical, C32, N, r);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      bw_add_du_c_f32_kernel<<<1216, 256, sizeof(float) * (size_t)r * 64, st>>>(C32, L.Cm, r, dY32, N, M, r);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (dxtype == PYLOM_F32)
+      bw_finalize_kernel<float, float><<<1024, 256, 0, st>>>(dY32, w, remove_mean, (float*)dX, lddx, N, M);
+    else
+      bw_finalize_kernel<double, float><<<1024, 256, 0, st>>>(dY32, w, remove_mean, (double*)dX, lddx, N, M);
+    return cudaGetLastError();
+  }
   if ((e = launch_modes_fp64(ds, L.Bm, M, M, nullptr, 0, L.dY, N, nullptr, st)) != cudaSuccess) return e;
   // ... + dU_w C (dU reloaded: step 1 transformed its copy in place)
   if (dU && r > 0) {
@@ -304,9 +368,9 @@ cudaError_t launch_pod_backward(const TsqrState& fs, const double* UR, const dou
   }
   // 4. dX = W^(1/2) dY (minus row means)
   if (dxtype == PYLOM_F32)
-    bw_finalize_kernel<float><<<1024, 256, 0, st>>>(L.dY, w, remove_mean, (float*)dX, lddx, N, M);
+    bw_finalize_kernel<float, double><<<1024, 256, 0, st>>>(L.dY, w, remove_mean, (float*)dX, lddx, N, M);
   else
-    bw_finalize_kernel<double><<<1024, 256, 0, st>>>(L.dY, w, remove_mean, (double*)dX, lddx, N, M);
+    bw_finalize_kernel<double, double><<<1024, 256, 0, st>>>(L.dY, w, remove_mean, (double*)dX, lddx, N, M);
   return cudaGetLastError();
 }
 

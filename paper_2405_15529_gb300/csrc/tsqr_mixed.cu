@@ -613,6 +613,51 @@ __global__ void __launch_bounds__(kMxThreads) modes_mixed_kernel(TsqrState s, co
   }
 }
 
+// Adjoint support: per leaf, C_leaf := Q_leaf^T C_leaf in FP32 on tcgen05
+// (panels in factorisation order, op(T) = T^T), then the leaf's top M rows
+// go to its binary64 slot Z (M x r, the start of the tree's bottom-up pass).
+__global__ void __launch_bounds__(kMxThreads) leaf_qt_mixed_kernel(TsqrState s, const float* Yf, const double* T2,
+                                                                  float* C, int64_t r, double* Z) {
+  extern __shared__ __align__(128) unsigned char msm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t leaf = blockIdx.x;
+  const int64_t r0 = leaf_begin(leaf, s.N, s.P);
+  const int64_t h = leaf_begin(leaf + 1, s.N, s.P) - r0;
+  const int64_t M = s.M;
+  const int64_t npan = (M + kNB2 - 1) / kNB2;
+  double* sT = (double*)(msm + kOffT);
+  if (tid == 0) tc05::mbar_init(&mbar, 1);
+  if (warp == 0) tc05::tmem_alloc(&tmem_base, kTmemCols);
+  tc05::fence_before();
+  __syncthreads();
+  tc05::fence_after();
+  const uint32_t tmem = tmem_base;
+  uint32_t phase = 0;
+  bool ok = true;
+  const float* Y = Yf + r0;
+  float* Cl = C + r0;
+  for (int64_t pan = 0; pan < npan && ok; ++pan) {
+    const int64_t k = pan * kNB2;
+    const int nbk = (int)((M - k) < kNB2 ? (M - k) : kNB2);
+    const double* Tg = T2 + (leaf * npan + pan) * kNB2 * kNB2;
+    for (int idx = tid; idx < kNB2 * kNB2; idx += blockDim.x) sT[idx] = Tg[idx];
+    __syncthreads();
+    ok = block_reflector_tc<true>(Y, s.N, k, nbk, h, Cl, s.N, (int)r, sT, msm, tmem, &mbar, phase);
+    __syncthreads();
+  }
+  tc05::fence_before();
+  __syncthreads();
+  if (warp == 0) tc05::tmem_dealloc(tmem, kTmemCols);
+  if (!ok) {
+    if (tid == 0) raise_status(s.hdr, PYLOM_ERR_TIMEOUT);
+    return;
+  }
+  double* Zl = Z + leaf * M * r;
+  for (int64_t idx = tid; idx < M * r; idx += blockDim.x) Zl[idx] = (double)Cl[(idx % M) + (idx / M) * s.N];
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -653,6 +698,22 @@ cudaError_t launch_modes_mixed(const TsqrState& s, char* extra, const double* Ur
   const float* Yf = (const float*)extra;
   const double* T2 = (const double*)(extra + align256(sizeof(float) * (size_t)s.N * s.M));
   modes_mixed_kernel<<<(unsigned)s.P, kMxThreads, kMixSmemTotal, st>>>(s, Yf, T2, r_fixed, w, physical, U, ldu, r_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_qt_mixed(const TsqrState& s, char* extra, float* C, int64_t r, double* Z, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(leaf_qt_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kMixSmemTotal);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(modes_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMixSmemTotal);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const float* Yf = (const float*)extra;
+  const double* T2 = (const double*)(extra + align256(sizeof(float) * (size_t)s.N * s.M));
+  leaf_qt_mixed_kernel<<<(unsigned)s.P, kMxThreads, kMixSmemTotal, st>>>(s, Yf, T2, C, r, Z);
   return cudaGetLastError();
 }
 

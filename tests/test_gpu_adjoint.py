@@ -138,3 +138,77 @@ def test_adjoint_full_size_matches_torch_svd_autograd():
     with torch.no_grad():
         rel = (torch.linalg.norm(G - Xr.grad) / torch.linalg.norm(Xr.grad)).item()
     assert rel <= 1e-4, rel
+
+
+# ---------------------------------------------------------------------------
+# mixed-precision forward (FP32 modes) and its tcgen05 adjoint
+# ---------------------------------------------------------------------------
+# FP32 storage and 3xTF32 products leave about 1e-7 relative error in the
+# modes; the gradient 2 sqrt(w) (I - U_r U_r^T) Y_w amplifies it by the
+# inverse gap (s_r - s_{r+1}) / s_max ~ 0.1 here, and by s_max over the tail
+# norm, so 1e-4 (relative Frobenius) leaves a wide margin.
+MIXED_GRAD = 1e-4
+
+
+def test_adjoint_mixed_matches_closed_form():
+    N, M, r = 512, 16, 4
+    X, w, s = synth.known_spectrum(N, M, weights=True, seeds=(7, 8, 9))
+    Xd = _dev(X).float().requires_grad_(True)
+    wd = torch.from_numpy(w).cuda()
+    U, S, VT = pg.pod_autograd(Xd, r, w=wd, remove_mean=False, leaf_rows=64, prec=pg.PREC_MIXED_3XTF32)
+    assert U.dtype == torch.float32
+    L = _loss_torch(Xd, wd, U.double())
+    L.backward()
+    G = Xd.grad.double().cpu().numpy()
+    _, G_ref = oracle.pod_loss_grad(Xd.detach().double().cpu().numpy(), r, w=w, remove_mean=False)
+    rel = np.linalg.norm(G - G_ref) / np.linalg.norm(G_ref)
+    assert rel <= MIXED_GRAD, rel
+
+
+@pytest.mark.parametrize("remove_mean", [False, True])
+def test_adjoint_mixed_matches_fp64_adjoint(remove_mean):
+    # general cotangents (dU, dS, dVT) through both adjoints on the same X
+    # distinct singular values, so the modes are unique up to sign on both
+    # paths, and one decade only: cotangents of every right vector couple all
+    # pairs through 1 / (s_j^2 - s_i^2), so the comparison needs every
+    # direction resolved at FP32 accuracy (a six-decade spectrum leaves the
+    # smallest ones a few percent accurate in FP32)
+    N, M, r = 20000, 48, 6
+    X = synth.known_spectrum(N, M, s=synth.spectrum(M, decades=1.0), weights=False,
+                             seeds=(21, 22, 23))[0].astype(np.float32)
+    Xd = _dev(X)
+    g = torch.Generator(device="cuda").manual_seed(11)
+    dU = torch.randn(N, r, dtype=torch.float64, device="cuda", generator=g)
+    dS = torch.randn(M, dtype=torch.float64, device="cuda", generator=g)
+    dVT = torch.randn(M, M, dtype=torch.float64, device="cuda", generator=g)
+    out = {}
+    for prec in (pg.PREC_FP64, pg.PREC_MIXED_3XTF32):
+        res = pg.pod(Xd, remove_mean=remove_mean, r_max=r, leaf_rows=2000, prec=prec)
+        out[prec] = pg.pod_backward(res, (N, M), None, remove_mean, pg.MODES_ORTHONORMAL, 2000, r,
+                                    dU=dU, dS=dS, dVT=dVT).double()
+        out[prec, "U"] = res.U.double()
+    # both forwards use the same sign rule, so the modes agree column by column
+    assert torch.allclose(out[pg.PREC_FP64, "U"], out[pg.PREC_MIXED_3XTF32, "U"], atol=1e-4)
+    a, b = out[pg.PREC_FP64], out[pg.PREC_MIXED_3XTF32]
+    rel = (torch.linalg.norm(a - b) / torch.linalg.norm(a)).item()
+    assert rel <= MIXED_GRAD, rel
+
+
+def test_adjoint_mixed_full_size_fp32():
+    # 4,194,304 x 256 float32 snapshots (six-decade spectrum, weights), r = 20
+    N, M, r = 1 << 22, 256, 20
+    XT, w, s = synth.known_spectrum_torch(N, M, device="cuda", dtype=torch.float32)
+    X = XT.t().detach().requires_grad_(True)
+    U, S, VT = pg.pod_autograd(X, r, w=w, remove_mean=False, prec=pg.PREC_MIXED_3XTF32)
+    L = _loss_torch(X, w, U.double())
+    L.backward()
+    G = X.grad
+    assert G.dtype == torch.float32
+    with torch.no_grad():
+        Ud = U.double()
+        Yw = X.double() * torch.sqrt(w)[:, None]
+        Gc = 2.0 * torch.sqrt(w)[:, None] * (Yw - Ud @ (Ud.T @ Yw))
+        rel = (torch.linalg.norm(G.double() - Gc) / torch.linalg.norm(Gc)).item()
+        tail = float(np.sum(S.cpu().numpy()[r:] ** 2))
+    assert rel <= MIXED_GRAD, rel
+    assert L.item() == pytest.approx(tail, rel=1e-5)
