@@ -203,6 +203,42 @@ pylom_status pylom_svd_small(const double* R, int64_t M, int64_t ldr, double* U,
                              void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
+ * SPOD front end (Sec. 2.3, Alg. 6): the matrices Q_f of every frequency.
+ * The snapshots D (N points x T instants) are cut into nBlks blocks of npwin
+ * instants overlapping by nolap (nBlks = floor((T - nolap)/(npwin - nolap)),
+ * block b starting at instant b (npwin - nolap)); optionally each point's
+ * temporal mean is removed; every point's block is multiplied by the
+ * Hamming window w_j = 0.54 - 0.46 cos(2 pi j/(npwin - 1)), j = 0..npwin-1,
+ * transformed (X_k = sum_j x_j w_j exp(-2 pi i k j / npwin)), divided by
+ * mean(w) npwin, and the one-sided spectrum k = 0 .. floor(npwin/2) keeps
+ * all entries but its first and last doubled (as Alg. 6 writes it).  Q_f
+ * gathers frequency f of every block, scaled by 1/sqrt(nBlks), so
+ * Q_f = U_f S_f V_f^H is the SVD that pylom_svd_batched_* computes and
+ * L_f = S_f^2 the SPOD energies; frequency f is f / (dt npwin).
+ *   pylom_spod_shape      nBlks and nfreq = floor(npwin/2) + 1 for T, npwin,
+ *                         nolap (2 <= npwin <= 512, 0 <= nolap < npwin,
+ *                         T >= npwin).
+ *   pylom_spod_blocks     D: device N x T (ldd >= N), dtype F32 or F64, not
+ *                         modified.  Q: device complex64, nfreq matrices of
+ *                         N x nBlks (column-major, ld ldq >= N), matrix f at
+ *                         Q + f * nBlks * ldq elements.  mean: device N
+ *                         doubles or NULL (written when remove_mean).
+ *                         Workspace: pylom_spod_blocks_workspace_size(N,
+ *                         npwin) bytes, 256-byte aligned.  FP32 arithmetic,
+ *                         the mean and the tables in binary64.  Capturable.
+ *   pylom_spod_order      order[i] = the frequency with the i-th largest
+ *                         leading energy S[f * stride]^2 (ties by index),
+ *                         S on the device (the packed S of the batched SVD,
+ *                         stride nBlks), order: device nfreq int64.
+ * ------------------------------------------------------------------------ */
+pylom_status pylom_spod_shape(int64_t T, int64_t npwin, int64_t nolap, int64_t* nblks, int64_t* nfreq);
+size_t pylom_spod_blocks_workspace_size(int64_t N, int64_t npwin);
+pylom_status pylom_spod_blocks(const void* D, int64_t N, int64_t T, int64_t ldd, int dtype, int64_t npwin,
+                               int64_t nolap, int remove_mean, void* Q, int64_t ldq, double* mean, void* ws,
+                               size_t ws_bytes, void* stream);
+pylom_status pylom_spod_order(const double* S, int64_t nfreq, int64_t stride, int64_t* order, void* stream);
+
+/* ------------------------------------------------------------------------
  * Batched complex SVDs -- the per-frequency SVDs of SPOD (Sec. 2.3, Alg. 6:
  * (1/sqrt(nBlks)) Q_f = U_f S_f V_f^H for every frequency bin f), all bins
  * in one cooperative persistent launch.  Each bin: TSQR with complex

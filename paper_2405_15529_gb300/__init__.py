@@ -39,6 +39,7 @@ EXPORTS = (
     "pylom_pod_backward_workspace_size", "pylom_pod_backward",
     "pylom_svd_batched_plan", "pylom_svd_batched_bind", "pylom_svd_batched_run",
     "pylom_svd_batched_plan_info", "pylom_svd_batched_plan_destroy",
+    "pylom_spod_shape", "pylom_spod_blocks_workspace_size", "pylom_spod_blocks", "pylom_spod_order",
 )
 PROFILE_PHASES = ("leaf_qr_tree", "svd_small", "down_pass", "modes")
 
@@ -98,6 +99,14 @@ def load_library(path: str = LIB_PATH):
     lib.pylom_pod_backward.restype = _int
     lib.pylom_pod_backward.argtypes = [_vp, _sz, _i64, _i64, _i64, _i64, _i64, _vp, _int, _int, _int, _vp, _vp,
                                        _i64, _vp, _i64, _vp, _vp, _i64, _vp, _i64, _int, _vp, _sz, _vp]
+    lib.pylom_spod_shape.restype = _int
+    lib.pylom_spod_shape.argtypes = [_i64, _i64, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+    lib.pylom_spod_blocks_workspace_size.restype = _sz
+    lib.pylom_spod_blocks_workspace_size.argtypes = [_i64, _i64]
+    lib.pylom_spod_blocks.restype = _int
+    lib.pylom_spod_blocks.argtypes = [_vp, _i64, _i64, _i64, _int, _i64, _i64, _int, _vp, _i64, _vp, _vp, _sz, _vp]
+    lib.pylom_spod_order.restype = _int
+    lib.pylom_spod_order.argtypes = [_vp, _i64, _i64, _vp, _vp]
     lib.pylom_svd_batched_plan.restype = _int
     lib.pylom_svd_batched_plan.argtypes = [_int, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                            _i64, _int, ctypes.POINTER(_vp), ctypes.POINTER(_sz)]
@@ -508,3 +517,100 @@ class BatchedSVD:
                 self.plan = None
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# SPOD (Sec. 2.3, Alg. 6): front end + batched SVDs + ordering
+# ---------------------------------------------------------------------------
+
+def spod_shape(T: int, npwin: int, nolap: int):
+    """(nBlks, nfreq) of Alg. 6 for T snapshots, windows of npwin overlapping by nolap."""
+    nb, nf = _i64(0), _i64(0)
+    _raise(load_library().pylom_spod_shape(int(T), int(npwin), int(nolap), ctypes.byref(nb), ctypes.byref(nf)),
+           "pylom_spod_shape")
+    return int(nb.value), int(nf.value)
+
+
+def spod_blocks(D, npwin: int, nolap: int, remove_mean: bool = True, Q=None, mean=None, workspace=None,
+                stream=None):
+    """The matrices Q_f / sqrt(nBlks) of every frequency (Alg. 6) from the
+    snapshots D (N x T CUDA tensor, float32 or float64): a complex64 tensor
+    Q of shape (nfreq, nBlks, N), Q[f].t() being the N x nBlks matrix of
+    frequency f (column-major)."""
+    torch = _torch()
+    lib = load_library()
+    D = _colmajor(D)
+    N, T = D.shape
+    dt = {torch.float32: F32, torch.float64: F64}.get(D.dtype)
+    if dt is None:
+        raise TypeError("D must be float32 or float64")
+    nblks, nfreq = spod_shape(T, npwin, nolap)
+    dev = D.device
+    if Q is None:
+        Q = torch.empty((nfreq, nblks, N), dtype=torch.complex64, device=dev)
+    need = lib.pylom_spod_blocks_workspace_size(N, int(npwin))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    _raise(lib.pylom_spod_blocks(_dptr(D), N, T, _ld(D), dt, int(npwin), int(nolap), int(bool(remove_mean)),
+                                 _dptr(Q), int(Q.shape[2]), _dptr(mean), _dptr(workspace), workspace.numel(),
+                                 _stream(stream)), "pylom_spod_blocks")
+    return Q
+
+
+class SPOD:
+    """SPOD of the snapshot matrix D (N points x T instants) on the GPU
+    (Sec. 2.3, Alg. 6): the front end (blocks, Hamming window, one-sided
+    transform, Q_f), the SVDs of all frequencies in one persistent launch,
+    and the order of the frequencies by their leading energy.  run() is
+    capturable as one CUDA graph (capture() / replay()).  After a run:
+    L (nfreq x nBlks energies S^2, bin order), modes[f] (N x kmodes complex64),
+    order (frequencies by leading energy), f (frequency axis, 1 / time)."""
+
+    def __init__(self, D, dt: float, npwin: int, nolap: int, remove_mean: bool = True, kmodes: int = 8,
+                 prec=PREC_MIXED_3XTF32, leaf_rows=None):
+        torch = _torch()
+        self.lib = load_library()
+        self.D = _colmajor(D)
+        N, T = self.D.shape
+        self.npwin, self.nolap, self.remove_mean = int(npwin), int(nolap), bool(remove_mean)
+        self.nblks, self.nfreq = spod_shape(T, npwin, nolap)
+        dev = self.D.device
+        self.Q = torch.empty((self.nfreq, self.nblks, N), dtype=torch.complex64, device=dev)
+        self.ws = torch.empty(self.lib.pylom_spod_blocks_workspace_size(N, self.npwin), dtype=torch.uint8,
+                              device=dev)
+        self.svd = BatchedSVD([self.Q[f].t() for f in range(self.nfreq)], kmodes=kmodes, prec=prec,
+                              leaf_rows=leaf_rows)
+        self.order = torch.empty(self.nfreq, dtype=torch.int64, device=dev)
+        self.f = torch.arange(self.nfreq, dtype=torch.float64, device=dev) / (float(dt) * self.npwin)
+        self.graph = None
+
+    def run(self, stream=None):
+        spod_blocks(self.D, self.npwin, self.nolap, self.remove_mean, Q=self.Q, workspace=self.ws, stream=stream)
+        self.svd.run(stream)
+        _raise(self.lib.pylom_spod_order(_dptr(self.svd.S_all), self.nfreq, self.nblks, _dptr(self.order),
+                                         _stream(stream)), "pylom_spod_order")
+
+    @property
+    def L(self):
+        return self.svd.S_all.view(self.nfreq, self.nblks) ** 2
+
+    @property
+    def modes(self):
+        return self.svd.modes
+
+    def status(self, stream=None):
+        return self.svd.status(stream)
+
+    def capture(self):
+        torch = _torch()
+        self.run()                       # warm-up outside capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run(torch.cuda.current_stream())
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
