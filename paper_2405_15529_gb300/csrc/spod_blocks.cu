@@ -7,16 +7,17 @@
 // Alg. 6 writes it) is gathered per frequency into Q_f (N x nBlks), scaled
 // by 1/sqrt(nBlks): the matrices whose SVDs the batched kernel computes.
 //
-// One thread per (point, block): the npwin windowed samples of its point
-// are staged in shared memory (column per thread, conflict-free), and every
-// frequency is a direct transform over them with the window and the
-// twiddle factors read from shared tables (any npwin, including the paper's
-// 60).  Reads of D are coalesced across the points of a block; each Q_f
+// For npwin <= 64 the transform runs on the tensor cores (below).  Larger
+// windows take the direct form: one thread per (point, block), the npwin
+// windowed samples of its point staged in shared memory (column per thread,
+// conflict-free), every frequency a direct transform over them with the
+// window and the twiddle factors read from shared tables.  Reads of D are coalesced across the points of a block; each Q_f
 // column is written coalesced.  FP32 arithmetic (the bins are complex64),
 // the temporal mean and the tables in binary64.
 #include <math.h>
 
 #include "kernels.h"
+#include "tc05.cuh"
 
 namespace pylom {
 
@@ -101,6 +102,144 @@ __global__ void __launch_bounds__(kSpodThreads) spod_blocks_kernel(const TD* D, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core form (npwin <= 64): the transform of a tile of 128 points is a
+// dense contraction Q_tile (128 x 2 nfreq) = X_tile (128 x npwin) F, with the
+// window, the one-sided doubling and the scaling folded into F:
+//   F[j][k]        =  c_k w_j cos(2 pi k j / npwin) / (mean(w) npwin sqrt(nBlks))
+//   F[j][kFIm + k] = -c_k w_j sin(2 pi k j / npwin) / (mean(w) npwin sqrt(nBlks))
+// (the imaginary parts at a fixed column offset, so the epilogue indexes
+// its registers statically).  3xTF32 on tcgen05 (hi*hi into one TMEM
+// accumulator, hi*lo + lo*hi into another), K = npwin padded to 64, N = kFN.
+// F is built once in binary64 (split hi/lo, core-matrix layout) by a setup
+// kernel; every CTA copies it to shared memory and loops over all blocks of
+// its 128 points.
+// ---------------------------------------------------------------------------
+constexpr int kFK = 64;          // K (samples), padded
+constexpr int kFN = 80;          // N: real parts in columns 0..32, imaginary parts in kFIm..kFIm+32
+constexpr int kFIm = kFN / 2;
+constexpr int kFThreads = 128;
+constexpr int kFA = 128 * kFK * 4;               // A tile (hi or lo): 32 KB
+constexpr int kFB = kFN * kFK * 4;               // F (hi or lo): 20 KB
+constexpr int kFSmem = 2 * kFA + 2 * kFB;        // 104 KB
+constexpr uint32_t kFTmem = 256;                 // 2 x kFN accumulator columns, rounded up
+
+// F in the K-major core-matrix layout, hi then lo (2 x kFB bytes of floats)
+__global__ void spod_ftab_kernel(float* Fhl, int64_t npwin, int64_t nblks) {
+  const int64_t nfreq = npwin / 2 + 1;
+  double wsum = 0.0;
+  for (int64_t j = 0; j < npwin; ++j) wsum += 0.54 - 0.46 * cos(2.0 * M_PI * (double)j / (double)(npwin - 1));
+  const double scale = 1.0 / (wsum * sqrt((double)nblks));
+  for (int idx = threadIdx.x; idx < kFN * kFK; idx += blockDim.x) {
+    const int n = idx / kFK, j = idx % kFK;    // F^T row n (output column), K index j
+    double v = 0.0;
+    const int64_t k = n < kFIm ? n : n - kFIm;
+    if (j < npwin && k < nfreq) {
+      const double c = (k > 0 && k < nfreq - 1) ? 2.0 : 1.0;
+      const double wj = 0.54 - 0.46 * cos(2.0 * M_PI * (double)j / (double)(npwin - 1));
+      const double a = 2.0 * M_PI * (double)((k * j) % npwin) / (double)npwin;
+      v = c * wj * scale * (n < kFIm ? cos(a) : -sin(a));
+    }
+    float hi, lo;
+    tc05::split_tf32((float)v, hi, lo);
+    const uint32_t o = tc05::cm_off(n, j, kFK) / 4;
+    Fhl[o] = hi;
+    Fhl[kFN * kFK + o] = lo;
+  }
+}
+
+template <typename TD>
+__global__ void __launch_bounds__(kFThreads) spod_dft_tc_kernel(const TD* D, int64_t N, int64_t ldd,
+                                                               const double* mean, const float* Fhl,
+                                                               int64_t npwin, int64_t nolap, int64_t nblks,
+                                                               float2* Q, int64_t ldq, WsHeader* hdr) {
+  using namespace tc05;
+  extern __shared__ __align__(128) unsigned char fsm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t p0 = (int64_t)blockIdx.x * 128;
+  // F (hi, lo) into shared memory
+  {
+    const float4* src = (const float4*)Fhl;
+    float4* dst = (float4*)(fsm + 2 * kFA);
+    for (int i = tid; i < 2 * kFB / 16; i += kFThreads) dst[i] = src[i];
+  }
+  if (tid == 0) mbar_init(&mbar, 1);
+  if (warp == 0) tmem_alloc(&tmem_base, kFTmem);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_base;
+  uint32_t phase = 0;
+  const int64_t p = p0 + tid;     // this thread's point (its row of A and of the result)
+  const bool live = p < N;
+  const double mu = (live && mean) ? mean[p] : 0.0;
+  const float muf = (float)mu;
+  const int64_t nfreq = npwin / 2 + 1;
+  bool ok = true;
+  for (int64_t b = 0; b < nblks && ok; ++b) {
+    const int64_t i0 = b * (npwin - nolap);
+    // A row p: samples i0 .. i0 + npwin - 1 (zeros in the K padding), split
+#pragma unroll 4
+    for (int j = 0; j < kFK; ++j) {
+      float x = 0.f;
+      if (live && j < npwin) {
+        if constexpr (sizeof(TD) == 4) x = D[p + (i0 + j) * ldd] - muf;
+        else x = (float)(D[p + (i0 + j) * ldd] - mu);
+      }
+      float hi, lo;
+      split_tf32(x, hi, lo);
+      const uint32_t o = cm_off(tid, j, kFK);
+      *(float*)(fsm + o) = hi;
+      *(float*)(fsm + kFA + o) = lo;
+    }
+    fence_smem_async();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (tid == 0) {
+      const uint32_t a_hi = smem_u32(fsm), a_lo = smem_u32(fsm + kFA);
+      const uint32_t b_hi = smem_u32(fsm + 2 * kFA), b_lo = smem_u32(fsm + 2 * kFA + kFB);
+      const uint32_t sbo = (kFK / 4) * 128, lbo = 128;
+      const uint32_t id = idesc_tf32(128, kFN);
+      for (int kk = 0; kk < kFK / 8; ++kk) {
+        const uint32_t o = (uint32_t)kk * 256;
+        mma_tf32(tmem, desc(a_hi + o, lbo, sbo), desc(b_hi + o, lbo, sbo), id, kk > 0);
+        mma_tf32(tmem + kFN, desc(a_hi + o, lbo, sbo), desc(b_lo + o, lbo, sbo), id, kk > 0);
+        mma_tf32(tmem + kFN, desc(a_lo + o, lbo, sbo), desc(b_hi + o, lbo, sbo), id, true);
+      }
+      commit(&mbar);
+    }
+    const bool w_ok = mbar_wait(&mbar, phase);
+    phase ^= 1u;
+    fence_after();
+    ok = !__syncthreads_or(!w_ok);
+    if (!ok) break;
+    // epilogue: row p of the accumulators -> Q_k[p, b] for every frequency k
+    const uint32_t lanebase = (uint32_t)(warp * 32) << 16;
+    float hh[16], xx[16], re[kFN];
+#pragma unroll
+    for (int c0 = 0; c0 < kFN; c0 += 16) {
+      tmem_ld16(tmem + lanebase + (uint32_t)c0, hh);
+      tmem_ld16(tmem + lanebase + (uint32_t)(kFN + c0), xx);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) re[c0 + j] = hh[j] + xx[j];
+    }
+    if (live) {
+#pragma unroll
+      for (int k = 0; k < kFIm; ++k)
+        if (k < nfreq) Q[(k * nblks + b) * ldq + p] = make_float2(re[k], re[kFIm + k]);
+    }
+    fence_before();
+    __syncthreads();
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kFTmem);
+  if (!ok && tid == 0) raise_status(hdr, PYLOM_ERR_TIMEOUT);
+}
+
 // order[i] = the bin with the i-th largest leading energy S[f stride]^2,
 // ties by index (one block; nfreq is small)
 __global__ void spod_order_kernel(const double* S, int64_t nfreq, int64_t stride, int64_t* order) {
@@ -138,7 +277,8 @@ extern "C" pylom_status pylom_spod_shape(int64_t T, int64_t npwin, int64_t nolap
 
 extern "C" size_t pylom_spod_blocks_workspace_size(int64_t N, int64_t npwin) {
   if (N < 1 || npwin < 2 || npwin > kSpodMaxWin) return 0;
-  return sizeof(WsHeader) + align256(sizeof(double) * (size_t)N) + align256(sizeof(float) * 3 * (size_t)npwin);
+  return sizeof(WsHeader) + align256(sizeof(double) * (size_t)N) + align256(sizeof(float) * 3 * (size_t)npwin) +
+         align256(2 * (size_t)kFB);
 }
 
 extern "C" pylom_status pylom_spod_blocks(const void* D, int64_t N, int64_t T, int64_t ldd, int dtype,
@@ -183,7 +323,31 @@ extern "C" pylom_status pylom_spod_blocks(const void* D, int64_t N, int64_t T, i
   }
   if (e == cudaSuccess && remove_mean && mean) e = cudaMemcpyAsync(mean, mu, sizeof(double) * (size_t)N,
                                                                     cudaMemcpyDeviceToDevice, st);
-  if (e == cudaSuccess) {
+  float* Fhl = (float*)((char*)tab + align256(sizeof(float) * 3 * (size_t)npwin));
+  if (e == cudaSuccess && npwin <= kFK) {
+    // tensor-core path
+    spod_ftab_kernel<<<1, 256, 0, st>>>(Fhl, npwin, nblks);
+    e = cudaGetLastError();
+    static bool tc_attr = false;
+    if (e == cudaSuccess && !tc_attr) {
+      e = cudaFuncSetAttribute(spod_dft_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFSmem);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(spod_dft_tc_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFSmem);
+      if (e == cudaSuccess) tc_attr = true;
+    }
+    if (e == cudaSuccess) {
+      const unsigned grid = (unsigned)((N + 127) / 128);
+      if (dtype == PYLOM_F32)
+        spod_dft_tc_kernel<float><<<grid, kFThreads, kFSmem, st>>>((const float*)D, N, ldd, remove_mean ? mu : nullptr,
+                                                                   Fhl, npwin, nolap, nblks, (float2*)Q, ldq,
+                                                                   (WsHeader*)base);
+      else
+        spod_dft_tc_kernel<double><<<grid, kFThreads, kFSmem, st>>>((const double*)D, N, ldd,
+                                                                    remove_mean ? mu : nullptr, Fhl, npwin, nolap,
+                                                                    nblks, (float2*)Q, ldq, (WsHeader*)base);
+      e = cudaGetLastError();
+    }
+  } else if (e == cudaSuccess) {
     const size_t smem = sizeof(float) * ((size_t)npwin * kSpodThreads + 3 * (size_t)npwin);
     static size_t smem_set = 0;
     if (smem > 48 * 1024 && smem > smem_set) {

@@ -37,6 +37,7 @@ def _waves(N, T, seed):
     (777, 301, 60, 30, False, torch.float32),   # the paper's window and overlap
     (129, 64, 64, 0, True, torch.float32),      # one block
     (300, 250, 15, 5, True, torch.float64),     # odd window
+    (500, 420, 100, 50, True, torch.float32),   # window above 64: the direct transform
 ])
 def test_spod_blocks_match_oracle(N, T, npwin, nolap, remove_mean, dtype):
     D = _waves(N, T, seed=N + T)
