@@ -281,6 +281,75 @@ def bench_spod_end_to_end(args, dev):
     return out
 
 
+def bench_streamed(args, dev):
+    """The out-of-core POD: the 4,194,304 x 256 known-spectrum matrix (float64,
+    8.6 GB) held in page-locked HOST memory and streamed through the device in
+    chunks of 304 leaves (about --stream-chunk rows); the modes return to host
+    memory.  Timed end to end (host to host) beside the in-core call with the
+    same leaf partition on a device-resident copy; the results must agree bit
+    for bit."""
+    import torch
+    import paper_2405_15529_gb300 as pg
+    import synth
+    N, M, chunk = args.rows, M_FULL, args.stream_chunk
+    XT, w, s = synth.known_spectrum_torch(N, M, device=dev)
+    b = pg.pod_streamed_leaf_rows(N, M, 0, chunk)
+    Xh = torch.empty((M, N), dtype=torch.float64, pin_memory=True)
+    Xh.copy_(XT)
+    Xh = Xh.t()
+    wh = w.cpu().reshape(-1, 1).pin_memory()      # N x 1: used in place (no per-call copy)
+    ref = pg.pod(XT.t(), w=w, remove_mean=False, energy=ENERGY, leaf_rows=b)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.stream_steps):
+        ref = pg.pod(XT.t(), w=w, remove_mean=False, energy=ENERGY, leaf_rows=b, workspace=ref.workspace)
+    torch.cuda.synchronize()
+    ms_in = (time.perf_counter() - t0) * 1e3 / args.stream_steps
+    S_ref, U_ref, r_ref = ref.S.clone(), ref.U.cpu(), ref.r
+    del ref, XT
+    torch.cuda.empty_cache()
+    Yh = torch.empty(N * M, dtype=torch.float64, pin_memory=True)
+    Uh = torch.empty((M, N), dtype=torch.float64, pin_memory=True).t()
+    res = pg.pod_streamed(Xh, w=wh, remove_mean=False, energy=ENERGY, leaf_rows=0, chunk_rows=chunk,
+                          host_scratch=Yh, out=Uh)
+    ws = res.workspace
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.stream_steps):
+        res = pg.pod_streamed(Xh, w=wh, remove_mean=False, energy=ENERGY, leaf_rows=0, chunk_rows=chunk,
+                              workspace=ws, host_scratch=Yh, out=Uh)
+    ms = (time.perf_counter() - t0) * 1e3 / args.stream_steps
+    equal = bool(res.r == r_ref and torch.equal(res.S, S_ref) and torch.equal(res.U, U_ref))
+    # the host link alone: one 2 GiB page-locked copy each way
+    hb = torch.empty(1 << 28, dtype=torch.float64, pin_memory=True)
+    db = torch.empty(1 << 28, dtype=torch.float64, device=dev)
+    link_gbs = {}
+    for name, dst, src in (("h2d", db, hb), ("d2h", hb, db)):
+        dst.copy_(src, non_blocking=True)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record()
+        dst.copy_(src, non_blocking=True)
+        c1.record()
+        torch.cuda.synchronize()
+        link_gbs[name] = hb.numel() * 8 / (c0.elapsed_time(c1) * 1e-3) / 1e9
+    del hb, db
+    P = pg.leaf_count(N, M, b)
+    link = N * M * 8 * 3 + N * res.r * 8 + N * 8     # X up, reflectors down and up, modes down, weights
+    out = {"workload": f"pod_known_spectrum_{N}x{M}_f64_host_resident", "ms_per_step": ms,
+           "steps": args.stream_steps, "value": N * M * 8 / (ms * 1e-3) / 1e9,
+           "unit": "GB/s of snapshots, host to host", "leaf_rows": b, "leaves": P,
+           "leaves_per_chunk": 304, "chunks": -(-P // 304), "device_workspace_gb": ws.numel() / 1e9,
+           "host_link_bytes_per_step": link, "host_link_gbs": link / (ms * 1e-3) / 1e9,
+           "link_copy_gbs_measured": link_gbs,
+           "bound_ms": max(ms_in, (N * M * 8 * 2 + N * res.r * 8) / (link_gbs["d2h"] * 1e9) * 1e3,
+                           N * M * 8 * 2 / (link_gbs["h2d"] * 1e9) * 1e3),
+           "in_core_same_partition_ms": ms_in, "streamed_over_in_core": ms / ms_in,
+           "r": res.r, "bitwise_equal_to_in_core": equal}
+    del res, ws, Xh, wh, Yh, Uh
+    torch.cuda.empty_cache()
+    return out
+
+
 C3_N, C3_M, C3_RMAX = 10_000_000, 1808, 128
 
 
@@ -605,6 +674,8 @@ def run_ours(args, rank, world, local_rank):
         extra["spod_batched"] = bench_spod(args, dev)
     if world == 1 and not args.no_spod:
         extra["spod_end_to_end"] = bench_spod_end_to_end(args, dev)
+    if world == 1 and not args.no_stream:
+        extra["streamed_host_resident"] = bench_streamed(args, dev)
     if world == 1 and not args.no_c3:
         extra["mixed_waves_1808"] = bench_waves_1808(args, dev)
 
@@ -654,6 +725,9 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-spod", action="store_true")
     ap.add_argument("--no-c3", action="store_true", help="skip the 10,000,000 x 1808 mixed-vs-FP64 section")
+    ap.add_argument("--no-stream", action="store_true", help="skip the host-resident (streamed) POD section")
+    ap.add_argument("--stream-chunk", type=int, default=1 << 20)
+    ap.add_argument("--stream-steps", type=int, default=2)
     ap.add_argument("--c3-rows", type=int, default=C3_N)
     ap.add_argument("--c3-steps", type=int, default=1)
     ap.add_argument("--adj-steps", type=int, default=3)

@@ -140,6 +140,45 @@ pylom_status pylom_pod(const void* X, int64_t N, int64_t M, int64_t ldx, int xty
                        void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
+ * pylom_pod_streamed -- pylom_pod (binary64 path) for a snapshot matrix in
+ * HOST memory that need not fit in device memory (the paper's largest
+ * datasets exceed any single device).  The leaves (the partition of
+ * pylom_leaf_count) are processed in chunks of whole leaves of at most
+ * about chunk_rows rows: pass 1 uploads each chunk of X (and w), runs the
+ * leaf QR with its mean / weight prologue and downloads the reflectors to
+ * the host scratch Yh; the tree, the small SVD, the truncation and the
+ * top-down pass run on the device; pass 2 uploads the reflectors again and
+ * downloads each chunk of U.  Two chunk buffers alternate and copies run on
+ * a second stream, so transfers overlap the kernels.  Results equal those
+ * of pylom_pod with the same leaf partition.
+ *  X      host N x M (ldx >= N), F32 or F64; w: host N doubles or NULL;
+ *  Yh     host scratch N x M doubles (ld N), overwritten;
+ *  U      host out N x r (ldu >= N, at least r_max columns);
+ *  S, VT  DEVICE out as in pylom_pod; mean: host N doubles or NULL;
+ *  r_out  host out, the truncation rank.
+ * Host buffers should be page-locked (cudaHostAlloc / cudaHostRegister)
+ * for the copies to overlap.  Synchronises `stream` once (to read r); on
+ * return the remaining work is queued on `stream`.  Device workspace:
+ * pylom_pod_streamed_workspace_size(N, M, leaf_rows, chunk_rows, r_max,
+ * xtype) bytes, 256-byte aligned.  Device statuses (non-finite input, ...)
+ * are returned directly.
+ *  leaf_rows = 0 sizes the leaves for the chunks: a chunk is 304 leaves
+ *  (two per SM, so every chunk launch fills the device) of
+ *  b = max(M, 1024, chunk_rows / 304) rows, and the results equal those of
+ *  pylom_pod with leaf_rows = b; pylom_pod_streamed_leaf_rows returns the b
+ *  a call uses (leaf_rows itself when > 0; -1 for a bad shape).  With
+ *  leaf_rows > 0 a chunk holds max(1, chunk_rows / (N / P)) leaves.
+ * ------------------------------------------------------------------------ */
+int64_t pylom_pod_streamed_leaf_rows(int64_t N, int64_t M, int64_t leaf_rows, int64_t chunk_rows);
+size_t pylom_pod_streamed_workspace_size(int64_t N, int64_t M, int64_t leaf_rows, int64_t chunk_rows,
+                                         int64_t r_max, int xtype);
+pylom_status pylom_pod_streamed(const void* X, int64_t N, int64_t M, int64_t ldx, int xtype, const double* w,
+                                int remove_mean, double energy, int64_t r_max, int mode_kind, int64_t leaf_rows,
+                                int64_t chunk_rows, double* Yh, double* U, int64_t ldu, double* S, double* VT,
+                                int64_t ldvt, double* mean, int64_t* r_out, void* ws, size_t ws_bytes,
+                                void* stream);
+
+/* ------------------------------------------------------------------------
  * pylom_pod_backward -- hand-written adjoint of pylom_pod (no counterpart in
  * the paper; it differentiates the composition of Alg. 2, Alg. 1 and Eqs.
  * svdqr1-svdqr3).  Given cotangents dU (of the r returned modes), dS and

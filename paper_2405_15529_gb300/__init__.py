@@ -40,6 +40,7 @@ EXPORTS = (
     "pylom_svd_batched_plan", "pylom_svd_batched_bind", "pylom_svd_batched_run",
     "pylom_svd_batched_plan_info", "pylom_svd_batched_plan_destroy",
     "pylom_spod_shape", "pylom_spod_blocks_workspace_size", "pylom_spod_blocks", "pylom_spod_order",
+    "pylom_pod_streamed_workspace_size", "pylom_pod_streamed", "pylom_pod_streamed_leaf_rows",
 )
 PROFILE_PHASES = ("leaf_qr_tree", "svd_small", "down_pass", "modes")
 
@@ -106,6 +107,13 @@ def load_library(path: str = LIB_PATH):
     lib.pylom_spod_blocks.restype = _int
     lib.pylom_spod_blocks.argtypes = [_vp, _i64, _i64, _i64, _int, _i64, _i64, _int, _vp, _i64, _vp, _vp, _sz, _vp]
     lib.pylom_spod_order.restype = _int
+    lib.pylom_pod_streamed_workspace_size.restype = _sz
+    lib.pylom_pod_streamed_workspace_size.argtypes = [_i64, _i64, _i64, _i64, _i64, _int]
+    lib.pylom_pod_streamed_leaf_rows.restype = _i64
+    lib.pylom_pod_streamed_leaf_rows.argtypes = [_i64, _i64, _i64, _i64]
+    lib.pylom_pod_streamed.restype = _int
+    lib.pylom_pod_streamed.argtypes = [_vp, _i64, _i64, _i64, _int, _vp, _int, _dbl, _i64, _int, _i64, _i64,
+                                       _vp, _vp, _i64, _vp, _vp, _i64, _vp, ctypes.POINTER(_i64), _vp, _sz, _vp]
     lib.pylom_spod_order.argtypes = [_vp, _i64, _i64, _vp, _vp]
     lib.pylom_svd_batched_plan.restype = _int
     lib.pylom_svd_batched_plan.argtypes = [_int, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
@@ -271,6 +279,94 @@ def pod(X, w=None, remove_mean=True, energy=0.0, r_max=None, mode_kind=MODES_ORT
         _raise(st, "pylom_pod (device)")
         U = U[:, :r]
     return PodResult(U=U, S=S, VT=VT, mean=mean, r=r, sweeps=sweeps, workspace=workspace, prec=int(prec))
+
+
+def pod_streamed_leaf_rows(N, M, leaf_rows=0, chunk_rows=1 << 22) -> int:
+    """Leaf height of a streamed POD call (its results equal pod() with this leaf_rows)."""
+    return int(load_library().pylom_pod_streamed_leaf_rows(N, M, leaf_rows, chunk_rows))
+
+
+@dataclass
+class StreamedPodResult:
+    U: "torch.Tensor"        # host N x r (column-major view of page-locked memory)
+    S: "torch.Tensor"        # device, M
+    VT: "torch.Tensor"       # device, M x M
+    mean: Optional["torch.Tensor"]   # host, N
+    r: int
+    workspace: "torch.Tensor"
+
+
+def _pinned_colmajor(A, dtype=None):
+    """A host column-major copy in page-locked memory (no copy if A already is one)."""
+    torch = _torch()
+    if not torch.is_tensor(A):
+        A = torch.as_tensor(A)
+    if dtype is not None and A.dtype != dtype:
+        A = A.to(dtype)
+    if A.device.type != "cpu":
+        raise ValueError("the streamed POD takes X in host memory")
+    if A.dim() != 2:
+        raise ValueError("expected a 2-D array")
+    rows, cols = A.shape
+    if (rows == 1 or A.stride(0) == 1) and (cols == 1 or A.stride(1) >= rows) and A.is_pinned():
+        return A
+    out = torch.empty((A.shape[1], A.shape[0]), dtype=A.dtype, pin_memory=True).t()
+    out.copy_(A)
+    return out
+
+
+def pod_streamed(X, w=None, remove_mean=True, energy=0.0, r_max=None, mode_kind=MODES_ORTHONORMAL,
+                 leaf_rows=0, chunk_rows=1 << 22, device=None, stream=None, workspace=None, host_scratch=None,
+                 out=None):
+    """POD (binary64 path) of an N x M snapshot matrix held in HOST memory,
+    streamed through the device in chunks of whole leaves of about
+    chunk_rows rows; the modes come back to host memory.  Same results as
+    pod() with the same leaf partition.  X: float32/float64 numpy array or
+    CPU tensor (copied to page-locked memory unless it already is).
+    host_scratch: page-locked float64 host tensor of at least N*M entries
+    (the leaves' reflectors between the passes); out: a page-locked
+    column-major float64 host tensor of N x >= r_max for the modes.  Both
+    are allocated per call when None (page-locking 2 N M doubles is slow:
+    pass them in for repeated calls)."""
+    torch = _torch()
+    lib = load_library()
+    X = _pinned_colmajor(X)
+    N, M = X.shape
+    xtype = {torch.float32: F32, torch.float64: F64}.get(X.dtype)
+    if xtype is None:
+        raise TypeError("X must be float32 or float64")
+    r_max = M if r_max is None else int(r_max)
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    if w is not None:
+        w = _pinned_colmajor(torch.as_tensor(w).to(torch.float64).reshape(-1, 1)).reshape(-1)
+    need = lib.pylom_pod_streamed_workspace_size(N, M, leaf_rows, chunk_rows, r_max, xtype)
+    if need == 0:
+        _raise(ERR_SHAPE, f"pylom_pod_streamed_workspace_size(N={N}, M={M}, b={leaf_rows}, "
+                          f"chunk={chunk_rows}, r_max={r_max})")
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    Yh = host_scratch
+    if Yh is None:
+        Yh = torch.empty(N * M, dtype=torch.float64, pin_memory=True)
+    elif Yh.dtype != torch.float64 or Yh.device.type != "cpu" or Yh.numel() < N * M or not Yh.is_contiguous():
+        raise ValueError("host_scratch must be a contiguous float64 host tensor of at least N*M entries")
+    U = out
+    if U is None:
+        U = torch.empty((r_max, N), dtype=torch.float64, pin_memory=True).t()
+    elif (U.dtype != torch.float64 or U.device.type != "cpu" or U.dim() != 2 or U.shape[0] != N
+          or U.shape[1] < r_max or U.stride(0) != 1):
+        raise ValueError("out must be a column-major float64 host tensor of N x >= r_max")
+    mean = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    S = torch.empty(M, dtype=torch.float64, device=dev)
+    VT = empty_colmajor(M, M, torch.float64, dev)
+    r = _i64(0)
+    st = lib.pylom_pod_streamed(_dptr(X), N, M, _ld(X), xtype, _dptr(w), int(bool(remove_mean)), float(energy),
+                                r_max, int(mode_kind), int(leaf_rows), int(chunk_rows), _dptr(Yh), _dptr(U), _ld(U),
+                                _dptr(S), _dptr(VT), _ld(VT), _dptr(mean), ctypes.byref(r), _dptr(workspace),
+                                workspace.numel(), _stream(stream))
+    _raise(st, "pylom_pod_streamed")
+    (stream if stream is not None else torch.cuda.current_stream()).synchronize()
+    return StreamedPodResult(U=U[:, :int(r.value)], S=S, VT=VT, mean=mean, r=int(r.value), workspace=workspace)
 
 
 def tsqr(A, leaf_rows=0, want_q=True, prec=PREC_FP64, stream=None, check=True):

@@ -33,7 +33,9 @@ constexpr int64_t kMinAutoLeafRows = 1024;
 
 // P = max(1, floor(N / b)) for a given leaf height b; automatic choice:
 // P = min(304, floor(N / max(M, 1024))) (152 for the mixed path), at least 1.
-int64_t leaves_of(int64_t N, int64_t M, int64_t leaf_rows, int prec = PYLOM_PREC_FP64) {
+}  // namespace
+
+int64_t pylom::leaves_of(int64_t N, int64_t M, int64_t leaf_rows, int prec) {
   int64_t P;
   if (leaf_rows > 0) {
     P = N / leaf_rows;
@@ -46,9 +48,11 @@ int64_t leaves_of(int64_t N, int64_t M, int64_t leaf_rows, int prec = PYLOM_PREC
   return P < 1 ? 1 : P;
 }
 
-bool tall_shape_ok(int64_t N, int64_t M, int64_t leaf_rows) {
+bool pylom::tall_shape_ok(int64_t N, int64_t M, int64_t leaf_rows) {
   return M >= 1 && M <= kMaxM && N >= M && (leaf_rows == 0 || leaf_rows >= M);
 }
+
+namespace {
 
 cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
 

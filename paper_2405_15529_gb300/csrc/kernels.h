@@ -28,6 +28,11 @@ struct TsqrState {
   int64_t rmax;
   double* Tt;               // 2 x ceil(P/2) x kNB x kNB: panel T factors of the cooperative tree
   int climb;                // 1: leaves run the last-arriver tree; 0: tree_coop_kernel follows them
+  // leaf kernels of a streamed problem run on a slice of the leaves whose
+  // rows sit in a device chunk: leaves leaf0 .. leaf0 + Pl - 1, buffer row 0
+  // = global row row0, Y (and X, w, mean, U) chunks with leading dimension
+  // ldy.  In-core: leaf0 = 0, Pl = P, row0 = 0, ldy = N.
+  int64_t leaf0, Pl, row0, ldy;
 };
 
 struct SvdState {
@@ -100,6 +105,17 @@ cudaError_t launch_leaf_qt_mixed(const TsqrState& s, char* extra, float* C, int6
 
 // Records a message for pylom_last_error() on the calling host thread.
 void set_error_message(const char* fmt, ...);
+
+// Leaf count of a problem (the rule of pylom_leaf_count; the mixed path caps
+// the automatic choice at one leaf per SM) and the shape check of the
+// tall-skinny entry points (api.cu).
+int64_t leaves_of(int64_t N, int64_t M, int64_t leaf_rows, int prec = PYLOM_PREC_FP64);
+bool tall_shape_ok(int64_t N, int64_t M, int64_t leaf_rows);
+
+// The leaves' modes product alone (after the top-down pass), for the leaf
+// slice of s (streamed problems).
+cudaError_t launch_leaf_modes_fp64(const TsqrState& s, int64_t r_fixed, const double* w, int physical, double* U,
+                                   int64_t ldu, int64_t* r_out, cudaStream_t st);
 
 // Top-down pass only (B_root from Ur or the identity, then every tree level).
 cudaError_t launch_down_pass_fp64(const TsqrState& s, const double* Ur, int64_t ldur, int64_t r_fixed,

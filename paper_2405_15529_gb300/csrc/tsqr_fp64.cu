@@ -111,7 +111,7 @@ __device__ void leaf_prologue(const LeafArgs& a, double* A, int64_t lda, int64_t
   const int64_t M = a.s.M;
   int bad = 0;
   for (int64_t i = threadIdx.x; i < h; i += blockDim.x) {
-    const int64_t n = r0 + i;
+    const int64_t n = r0 + i - a.s.row0;   // row in the (chunk) buffers
     double xbar = 0.0;
     if (a.remove_mean) {
       double sum = 0.0;
@@ -143,11 +143,11 @@ __global__ void __launch_bounds__(kLeafThreads) leaf_qr_kernel(LeafArgs a) {
   double* sWp = sW + kSmW;
   const TsqrState& s = a.s;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int64_t leaf = blockIdx.x;
+  const int64_t leaf = s.leaf0 + blockIdx.x;
   const int64_t r0 = leaf_begin(leaf, s.N, s.P);
   const int64_t h = leaf_begin(leaf + 1, s.N, s.P) - r0;
-  const int64_t M = s.M, lda = s.N;
-  double* A = s.Y + r0;
+  const int64_t M = s.M, lda = s.ldy;
+  double* A = s.Y + (r0 - s.row0);
 
   if (a.xtype == PYLOM_F32)
     leaf_prologue<float>(a, A, lda, r0, h);
@@ -235,31 +235,31 @@ __global__ void __launch_bounds__(kLeafThreads) modes_kernel(TsqrState s, int64_
   double* sW = sT + kSmT + kSmRed + kSmOut;
   double* sWp = sW + kSmW;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int64_t leaf = blockIdx.x;
+  const int64_t leaf = s.leaf0 + blockIdx.x;
   const int64_t r0 = leaf_begin(leaf, s.N, s.P);
   const int64_t h = leaf_begin(leaf + 1, s.N, s.P) - r0;
   const int64_t M = s.M;
   const int64_t r = (r_fixed >= 0) ? r_fixed : s.hdr->r;
   if (leaf == 0 && tid == 0 && r_out) *r_out = r;
-  double* C = U + r0;
+  double* C = U + (r0 - s.row0);
   const double* Bl = s.B + leaf * M * s.rmax;
   for (int64_t c = 0; c < r; ++c)
     for (int64_t i = tid; i < h; i += nthr) C[i + c * ldu] = (i < M) ? Bl[i + c * M] : 0.0;
   __syncthreads();
-  const double* A = s.Y + r0;
+  const double* A = s.Y + (r0 - s.row0);
   for (int64_t pan = s.npan - 1; pan >= 0; --pan) {
     const int64_t k = pan * kNB;
     const int nbk = (int)((M - k) < kNB ? (M - k) : kNB);
     const double* Tg = s.T + (leaf * s.npan + pan) * kSmT;
     for (int idx = tid; idx < kSmT; idx += nthr) sT[idx] = Tg[idx];
     __syncthreads();
-    LeafV V{A, s.N, k, h, nbk};
+    LeafV V{A, s.ldy, k, h, nbk};
     block_reflector<false, false>(V, nbk, k, h, C, ldu, (int)r, nullptr, 0, sT, sW, sWp);
     __syncthreads();
   }
   if (physical && w) {
     for (int64_t i = tid; i < h; i += nthr) {
-      const double iw = 1.0 / sqrt(w[r0 + i]);
+      const double iw = 1.0 / sqrt(w[r0 - s.row0 + i]);
       for (int64_t c = 0; c < r; ++c) C[i + c * ldu] *= iw;
     }
   }
@@ -320,6 +320,10 @@ void tsqr_state_carve(TsqrState& s, char* base, int64_t N, int64_t M, int64_t P,
   s.Tt = (double*)p;       p += align256(sizeof(double) * (size_t)2 * ((P + 1) / 2) * kSmT);
   s.B = rmax > 0 ? (double*)p : nullptr;
   s.climb = use_climb_tree(M, P) ? 1 : 0;
+  s.leaf0 = 0;
+  s.Pl = P;
+  s.row0 = 0;
+  s.ldy = N;
 }
 
 cudaError_t launch_tsqr_fp64(const TsqrState& s, const void* X, int64_t ldx, int xtype,
@@ -336,9 +340,11 @@ cudaError_t launch_tsqr_fp64(const TsqrState& s, const void* X, int64_t ldx, int
     attr_set = true;
   }
   LeafArgs a{s, X, ldx, xtype, w, remove_mean, mean};
-  leaf_qr_kernel<<<(unsigned)s.P, kLeafThreads, kLeafSmemBytes, st>>>(a);
+  leaf_qr_kernel<<<(unsigned)s.Pl, kLeafThreads, kLeafSmemBytes, st>>>(a);
   e = cudaGetLastError();
-  if (e != cudaSuccess || s.climb) return e;
+  // a launch over a slice of the leaves (streamed) leaves the cooperative
+  // tree to its caller, after the last slice
+  if (e != cudaSuccess || s.climb || s.Pl != s.P) return e;
   return launch_tree_coop(s, st);
 }
 
@@ -374,8 +380,21 @@ cudaError_t launch_modes_fp64(const TsqrState& s, const double* Ur, int64_t ldur
     e = cudaEventRecord(mid, st);
     if (e != cudaSuccess) return e;
   }
-  modes_kernel<<<(unsigned)s.P, kLeafThreads, kLeafSmemBytes, st>>>(s, r_fixed, w, physical, U, ldu,
-                                                                    r_out);
+  modes_kernel<<<(unsigned)s.Pl, kLeafThreads, kLeafSmemBytes, st>>>(s, r_fixed, w, physical, U, ldu,
+                                                                     r_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_modes_fp64(const TsqrState& s, int64_t r_fixed, const double* w, int physical, double* U,
+                                   int64_t ldu, int64_t* r_out, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(modes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kLeafSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  modes_kernel<<<(unsigned)s.Pl, kLeafThreads, kLeafSmemBytes, st>>>(s, r_fixed, w, physical, U, ldu, r_out);
   return cudaGetLastError();
 }
 
