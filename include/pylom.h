@@ -47,7 +47,8 @@ typedef enum {
   PYLOM_ERR_NONFINITE = 5,   /* device: the input holds NaN or Inf */
   PYLOM_ERR_NOCONV = 6,      /* device: Jacobi SVD hit max_sweeps */
   PYLOM_ERR_TIMEOUT = 7,     /* device: a bounded inter-block wait ran out */
-  PYLOM_ERR_UNSUPPORTED = 8  /* valid request this build does not implement */
+  PYLOM_ERR_UNSUPPORTED = 8, /* valid request this build does not implement */
+  PYLOM_ERR_SINGULAR = 9     /* device: a matrix that must be positive definite is not (DMD amplitudes) */
 } pylom_status;
 
 typedef enum { PYLOM_F32 = 0, PYLOM_F64 = 1, PYLOM_C64 = 2, PYLOM_C128 = 3 } pylom_dtype;
@@ -138,6 +139,45 @@ pylom_status pylom_pod(const void* X, int64_t N, int64_t M, int64_t ldx, int xty
                        void* U, int64_t ldu, double* S, double* VT, int64_t ldvt,
                        double* mean, int64_t* r_out, int prec,
                        void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * pylom_dmd -- exact dynamic mode decomposition with optimal amplitudes
+ * (Sec. 3.2, Alg. 3; amplitudes Alg. 5; the product U^T Y2 of Alg. 4).
+ *   Y = X - mean (each point's mean over all M snapshots, if remove_mean),
+ *   Y1 = Y[:, :M-1], Y2 = Y[:, 1:], Y1 = U S V^T truncated to r,
+ *   A = U^T Y2 V S^-1 (r x r), A w = w diag(mu),
+ *   phi = Y2 V S^-1 w diag(mu)^-1 (exact DMD modes),
+ *   b minimising || S V^T - w diag(b) V_and ||_F, V_and[i, t] = mu_i^t,
+ *   modes ordered by |b| descending (a conjugate pair shares the larger |b|
+ *   of its members, stays adjacent, positive imaginary part first).
+ * One TSQR of Y serves both Y1 and Y2 (Y1's QR is the leading part of Y's),
+ * so X is read once and the small steps run on matrices of <= M rows.
+ *  X      device N x M (ldx >= N), F32 or F64; 2 <= M <= 4096, N >= M.
+ *  energy, r_max  truncation of the SVD of Y1 as in pylom_pod (1 <= r_max
+ *         <= M-1); r is further cut to the numerical rank of Y1 (singular
+ *         values above max(N, M-1) 2^-52 s_1), so S^-1 exists.
+ *  mu, b  device out, 2 r_max doubles each: (re, im) of the sorted
+ *         eigenvalues and amplitudes.
+ *  Phi    device out N x r_max doubles (ldphi >= N), the sorted modes in
+ *         the packed real layout: a real eigenvalue's mode is one column;
+ *         a conjugate pair (mu_p, mu_p+1 = conj mu_p) stores Re phi_p in
+ *         column p and Im phi_p in column p+1 (phi_p+1 = conj phi_p).
+ *         Eigenvectors w are normalised to unit norm with their first
+ *         entry of largest modulus real and positive.
+ *  S      device out, the M-1 singular values of Y1.
+ *  mean   device out N doubles or NULL.  r_out: device int64, the rank r.
+ *  leaf_rows as in pylom_pod.  Device statuses (read with
+ *  pylom_workspace_status): PYLOM_ERR_NONFINITE, PYLOM_ERR_NOCONV (the
+ *  SVD, or the eigenvalue QR after 60 r + 100 double-shift steps),
+ *  PYLOM_ERR_SINGULAR (P of the amplitudes not positive definite, e.g.
+ *  repeated eigenvalues).  Asynchronous on `stream`; workspace:
+ *  pylom_dmd_workspace_size(N, M, leaf_rows, r_max, xtype) bytes,
+ *  256-byte aligned.
+ * ------------------------------------------------------------------------ */
+size_t pylom_dmd_workspace_size(int64_t N, int64_t M, int64_t leaf_rows, int64_t r_max, int xtype);
+pylom_status pylom_dmd(const void* X, int64_t N, int64_t M, int64_t ldx, int xtype, int remove_mean, double energy,
+                       int64_t r_max, int64_t leaf_rows, double* mu, double* b, double* Phi, int64_t ldphi,
+                       double* S, double* mean, int64_t* r_out, void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
  * pylom_pod_streamed -- pylom_pod (binary64 path) for a snapshot matrix in

@@ -32,8 +32,8 @@ objective):
   * the sort: a conjugate pair shares the larger |b| of its two members,
     stays adjacent, and the member with positive imaginary part comes first
     (the paper reorders conjugate pairs by the sign of the imaginary part);
-  * S^-1 needs s_k > 0: r is cut to the numerical rank of Y1's triangular
-    factor, the count of s_k > (M-1) 2^-52 s_1;
+  * S^-1 needs s_k > 0: r is cut to the numerical rank of Y1 by the usual
+    rule for an N x (M-1) matrix, the count of s_k > max(N, M-1) 2^-52 s_1;
   * eigenvectors: unit Euclidean norm, and the entry of largest modulus
     (the first such entry) made real and positive.
 """
@@ -46,12 +46,12 @@ import oracle
 EPS = 2.0 ** -52
 
 
-def numerical_rank(S, m1: int) -> int:
-    """Count of singular values above m1 * 2^-52 * s_1 (S sorted descending)."""
+def numerical_rank(S, dim: int) -> int:
+    """Count of singular values above dim * 2^-52 * s_1 (S sorted descending)."""
     S = np.asarray(S, dtype=np.float64)
     if S.size == 0 or S[0] <= 0.0:
         return 0
-    return int(np.sum(S > m1 * EPS * S[0]))
+    return int(np.sum(S > dim * EPS * S[0]))
 
 
 def normalize_eigvecs(W):
@@ -127,7 +127,7 @@ def dmd(D, energy: float = 0.0, r_max=None, remove_mean: bool = True):
         r_max = m1
     pod = oracle.pod(np.asfortranarray(Y1), remove_mean=False, energy=energy, r_max=r_max)
     S_all = pod["S"]
-    r = min(pod["r"], numerical_rank(S_all, m1))
+    r = min(pod["r"], numerical_rank(S_all, max(N, m1)))
     U, S, VT = pod["U"][:, :r], S_all[:r], pod["VT"][:r, :]
     if r == 0:
         z = np.zeros(0, dtype=np.complex128)

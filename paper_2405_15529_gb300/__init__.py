@@ -21,9 +21,10 @@ LIB_PATH = os.path.join(_HERE, "libpylom.so")
 
 # pylom_status
 OK, ERR_ARG, ERR_SHAPE, ERR_WORKSPACE, ERR_CUDA, ERR_NONFINITE, ERR_NOCONV, ERR_TIMEOUT, \
-    ERR_UNSUPPORTED = range(9)
+    ERR_UNSUPPORTED, ERR_SINGULAR = range(10)
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_SHAPE", 3: "ERR_WORKSPACE", 4: "ERR_CUDA",
-                5: "ERR_NONFINITE", 6: "ERR_NOCONV", 7: "ERR_TIMEOUT", 8: "ERR_UNSUPPORTED"}
+                5: "ERR_NONFINITE", 6: "ERR_NOCONV", 7: "ERR_TIMEOUT", 8: "ERR_UNSUPPORTED",
+                9: "ERR_SINGULAR"}
 # pylom_dtype / pylom_prec / pylom_mode_kind
 F32, F64, C64, C128 = 0, 1, 2, 3
 PREC_FP64, PREC_MIXED_3XTF32 = 0, 1
@@ -41,6 +42,7 @@ EXPORTS = (
     "pylom_svd_batched_plan_info", "pylom_svd_batched_plan_destroy",
     "pylom_spod_shape", "pylom_spod_blocks_workspace_size", "pylom_spod_blocks", "pylom_spod_order",
     "pylom_pod_streamed_workspace_size", "pylom_pod_streamed", "pylom_pod_streamed_leaf_rows",
+    "pylom_dmd_workspace_size", "pylom_dmd",
 )
 PROFILE_PHASES = ("leaf_qr_tree", "svd_small", "down_pass", "modes")
 
@@ -109,6 +111,11 @@ def load_library(path: str = LIB_PATH):
     lib.pylom_spod_order.restype = _int
     lib.pylom_pod_streamed_workspace_size.restype = _sz
     lib.pylom_pod_streamed_workspace_size.argtypes = [_i64, _i64, _i64, _i64, _i64, _int]
+    lib.pylom_dmd_workspace_size.restype = _sz
+    lib.pylom_dmd_workspace_size.argtypes = [_i64, _i64, _i64, _i64, _int]
+    lib.pylom_dmd.restype = _int
+    lib.pylom_dmd.argtypes = [_vp, _i64, _i64, _i64, _int, _int, _dbl, _i64, _i64, _vp, _vp, _vp, _i64, _vp, _vp,
+                              _vp, _vp, _sz, _vp]
     lib.pylom_pod_streamed_leaf_rows.restype = _i64
     lib.pylom_pod_streamed_leaf_rows.argtypes = [_i64, _i64, _i64, _i64]
     lib.pylom_pod_streamed.restype = _int
@@ -279,6 +286,84 @@ def pod(X, w=None, remove_mean=True, energy=0.0, r_max=None, mode_kind=MODES_ORT
         _raise(st, "pylom_pod (device)")
         U = U[:, :r]
     return PodResult(U=U, S=S, VT=VT, mean=mean, r=r, sweeps=sweeps, workspace=workspace, prec=int(prec))
+
+
+@dataclass
+class DmdResult:
+    mu: "torch.Tensor"          # r complex eigenvalues (sorted)
+    b: "torch.Tensor"           # r complex amplitudes
+    Phi_packed: "torch.Tensor"  # N x r real (conjugate pairs as Re / Im columns)
+    S: "torch.Tensor"           # M-1 singular values of Y1
+    mean: Optional["torch.Tensor"]
+    r: int
+    workspace: "torch.Tensor"
+
+    @property
+    def Phi(self):
+        """The modes as an N x r complex tensor (a layout change of Phi_packed)."""
+        torch = _torch()
+        mu = self.mu
+        P = self.Phi_packed
+        out = torch.empty((P.shape[0], self.r), dtype=torch.complex128, device=P.device)
+        p = 0
+        im = mu.imag.cpu()
+        while p < self.r:
+            if im[p] > 0.0:
+                out[:, p] = torch.complex(P[:, p], P[:, p + 1])
+                out[:, p + 1] = torch.complex(P[:, p], -P[:, p + 1])
+                p += 2
+            else:
+                out[:, p] = torch.complex(P[:, p], torch.zeros_like(P[:, p]))
+                p += 1
+        return out
+
+
+def dmd_workspace_size(N, M, leaf_rows=0, r_max=None, xtype=F64) -> int:
+    r_max = M - 1 if r_max is None else r_max
+    return int(load_library().pylom_dmd_workspace_size(N, M, leaf_rows, r_max, xtype))
+
+
+def dmd(X, remove_mean=True, energy=0.0, r_max=None, leaf_rows=0, workspace=None, out=None, stream=None,
+        check=True) -> DmdResult:
+    """Exact DMD of the N x M snapshot matrix X (Alg. 3, amplitudes of
+    Alg. 5) on the GPU.  X: CUDA tensor, float32 or float64.  With
+    check=False the call stays asynchronous (r is read later from the
+    workspace; the outputs then hold r_max entries)."""
+    torch = _torch()
+    lib = load_library()
+    X = _colmajor(X)
+    N, M = X.shape
+    xtype = {torch.float32: F32, torch.float64: F64}.get(X.dtype)
+    if xtype is None:
+        raise TypeError("X must be float32 or float64")
+    r_max = M - 1 if r_max is None else int(r_max)
+    dev = X.device
+    need = lib.pylom_dmd_workspace_size(N, M, leaf_rows, r_max, xtype)
+    if need == 0:
+        _raise(ERR_SHAPE, f"pylom_dmd_workspace_size(N={N}, M={M}, b={leaf_rows}, r_max={r_max})")
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    if out is None:
+        mu = torch.empty(2 * r_max, dtype=torch.float64, device=dev)
+        b = torch.empty(2 * r_max, dtype=torch.float64, device=dev)
+        Phi = empty_colmajor(N, r_max, torch.float64, dev)
+        S = torch.empty(max(M - 1, 1), dtype=torch.float64, device=dev)
+        mean = torch.empty(N, dtype=torch.float64, device=dev)
+        r_dev = torch.zeros(1, dtype=torch.int64, device=dev)
+    else:
+        mu, b, Phi, S, mean, r_dev = out
+    st = lib.pylom_dmd(_dptr(X), N, M, _ld(X), xtype, int(bool(remove_mean)), float(energy), r_max, int(leaf_rows),
+                       _dptr(mu), _dptr(b), _dptr(Phi), _ld(Phi), _dptr(S), _dptr(mean), _dptr(r_dev),
+                       _dptr(workspace), workspace.numel(), _stream(stream))
+    _raise(st, "pylom_dmd")
+    r = r_max
+    if check:
+        st, r, _ = workspace_status(workspace, stream)
+        _raise(st, "pylom_dmd (device)")
+    muc = torch.view_as_complex(mu.view(-1, 2))[:r]
+    bc = torch.view_as_complex(b.view(-1, 2))[:r]
+    return DmdResult(mu=muc, b=bc, Phi_packed=Phi[:, :r], S=S, mean=mean if remove_mean else None, r=r,
+                     workspace=workspace)
 
 
 def pod_streamed_leaf_rows(N, M, leaf_rows=0, chunk_rows=1 << 22) -> int:

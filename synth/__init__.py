@@ -248,3 +248,72 @@ def spod_bin_torch(N: int, Nb: int, seed: int, device, n_waves: int = 4, noise: 
                                torch.randn((N, Nb), dtype=torch.float64, device=device, generator=gen)) / math.sqrt(2.0)
     X /= math.sqrt(Nb)
     return X.T.contiguous().to(torch.complex64)
+
+
+# ----------------------------------------------------------------------------
+# oscillation workload (DMD)
+# ----------------------------------------------------------------------------
+
+def oscillation_params(K: int, seed: int = 0, rho_lo: float = 0.985, rho_hi: float = 1.0):
+    """K eigenvalues lambda_k = rho_k exp(i theta_k) with theta_k spread over
+    (0.05, 3.0) and rho_k in [rho_lo, rho_hi], and amplitudes a_k with
+    distinct moduli 1 + k / K (phases random)."""
+    rng = np.random.default_rng(seed)
+    theta = np.linspace(0.05, 3.0, K)
+    rho = rho_lo + (rho_hi - rho_lo) * rng.random(K)
+    lam = rho * np.exp(1j * theta)
+    amp = (1.0 + np.arange(K) / K) * np.exp(2j * np.pi * rng.random(K))
+    return lam, amp
+
+
+def oscillations(N: int, M: int, lams, amps, seed: int = 0, noise: float = 0.0, offset: float = 0.0):
+    """D[:, t] = offset + sum_k Re(a_k psi_k lambda_k^t) + noise (numpy,
+    Fortran order), psi_k with independent standard normal real and
+    imaginary parts.  Noise-free, D has rank 2K and its DMD is known in
+    closed form: eigenvalues lambda_k and conj(lambda_k), and each mode
+    times its amplitude equals a_k psi_k / 2 (or its conjugate).  Returns
+    (D, parts) with parts[k] = a_k psi_k / 2."""
+    rng = np.random.default_rng(seed)
+    t = np.arange(M)
+    D = np.full((N, M), float(offset), dtype=np.float64, order="F")
+    parts = []
+    for lam, a in zip(lams, amps):
+        psi = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+        D += np.real(a * psi[:, None] * np.asarray(lam) ** t[None, :])
+        parts.append(a * psi / 2.0)
+    if noise > 0.0:
+        D += noise * rng.standard_normal((N, M))
+    return np.asfortranarray(D), parts
+
+
+def oscillations_torch(N: int, M: int, lams, amps, seed: int, device, noise: float = 0.0, dtype=None,
+                       row_chunk: int = 1 << 21):
+    """Device-side :func:`oscillations` for large N: XT of shape (M, N)
+    (transpose view = the N x M matrix), built as Re(Psi C) with C[k, t] =
+    a_k lambda_k^t by library GEMMs.  Returns (XT, Psi_fn) where Psi_fn(rows)
+    regenerates psi for a row range (seeded per chunk) for closed-form checks."""
+    import torch
+    dtype = dtype or torch.float64
+    K = len(lams)
+    t = np.arange(M)
+    C = np.asarray(amps)[:, None] * np.asarray(lams)[:, None] ** t[None, :]
+    Cr = torch.tensor(C.real, dtype=torch.float64, device=device)
+    Ci = torch.tensor(C.imag, dtype=torch.float64, device=device)
+    XT = torch.empty((M, N), dtype=dtype, device=device)
+
+    def psi_chunk(r0, r1):
+        gen = torch.Generator(device=device)
+        gen.manual_seed(seed * 1000003 + r0)
+        pr = torch.randn((r1 - r0, K), dtype=torch.float64, device=device, generator=gen)
+        pi = torch.randn((r1 - r0, K), dtype=torch.float64, device=device, generator=gen)
+        nz = torch.randn((r1 - r0, M), dtype=torch.float64, device=device, generator=gen) if noise > 0 else None
+        return pr, pi, nz
+
+    for r0 in range(0, N, row_chunk):
+        r1 = min(N, r0 + row_chunk)
+        pr, pi, nz = psi_chunk(r0, r1)
+        blk = pr @ Cr - pi @ Ci
+        if nz is not None:
+            blk += noise * nz
+        XT[:, r0:r1] = blk.T.to(dtype)
+    return XT, psi_chunk
