@@ -112,10 +112,18 @@ __device__ void leaf_prologue(const LeafArgs& a, double* A, int64_t lda, int64_t
   int bad = 0;
   for (int64_t i = threadIdx.x; i < h; i += blockDim.x) {
     const int64_t n = r0 + i - a.s.row0;   // row in the (chunk) buffers
+    // kPro independent loads in flight per thread (the leaf has few warps)
+    constexpr int kPro = 16;
     double xbar = 0.0;
     if (a.remove_mean) {
       double sum = 0.0;
-      for (int64_t m = 0; m < M; ++m) sum += (double)X[n + m * a.ldx];
+      for (int64_t m0 = 0; m0 < M; m0 += kPro) {
+        double xv[kPro];
+#pragma unroll
+        for (int u = 0; u < kPro; ++u) xv[u] = (m0 + u < M) ? (double)X[n + (m0 + u) * a.ldx] : 0.0;
+#pragma unroll
+        for (int u = 0; u < kPro; ++u) sum += xv[u];
+      }
       xbar = sum / (double)M;
     }
     if (a.mean) a.mean[n] = xbar;
@@ -125,10 +133,17 @@ __device__ void leaf_prologue(const LeafArgs& a, double* A, int64_t lda, int64_t
       if (!(wn > 0.0) || !isfinite(wn)) bad = 1;
       sw = sqrt(wn);
     }
-    for (int64_t m = 0; m < M; ++m) {
-      const double x = (double)X[n + m * a.ldx];
-      if (!isfinite(x)) bad = 1;
-      A[i + m * lda] = sw * (x - xbar);
+    for (int64_t m0 = 0; m0 < M; m0 += kPro) {
+      double xv[kPro];
+#pragma unroll
+      for (int u = 0; u < kPro; ++u) xv[u] = (m0 + u < M) ? (double)X[n + (m0 + u) * a.ldx] : 0.0;
+#pragma unroll
+      for (int u = 0; u < kPro; ++u) {
+        if (m0 + u < M) {
+          if (!isfinite(xv[u])) bad = 1;
+          A[i + (m0 + u) * lda] = sw * (xv[u] - xbar);
+        }
+      }
     }
   }
   if (bad) raise_status(a.s.hdr, PYLOM_ERR_NONFINITE);

@@ -64,7 +64,7 @@ struct MixedArgs {
   TsqrState s;
   float* Yf;          // N x M fp32 working copy (ld N) -> reflectors
   double* T2;         // per leaf and panel: kNB2 x kNB2 (row-major) fp64
-  float* Pb;          // N x kNB2 row-major panel buffers (leaf rows)
+  float* Pb;          // panel scratch: (N / 128 + P + 1) chunk slots of kHrSlot floats
   const void* X;
   int64_t ldx;
   int xtype;
@@ -106,160 +106,345 @@ __device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
   return {s, e + a.c + b.c};
 }
 
-// Single-pass panel factorisation (columns [k, k+nbk) of the FP32 leaf) on
-// the row-major panel copy Pb (leaf rows k..h-1, 32 floats = 128 bytes per
-// row).  Pass jj, over the rows from the previous diagonal on:
-//   - finishes column jj-1: scales its sub-diagonal into the reflector
-//     v_{jj-1} = u / (alpha - beta) and applies (I - tau v v^T) to the later
-//     panel columns;
-//   - forms, from the still unscaled column jj (u below the diagonal), the
-//     squared norm sum u_i^2 and the dots sum u_i a_ic with every other
-//     panel column, as compensated FP32 sums.
-// Warp 0 then forms beta, tau and the scale of column jj in FP64 and the
-// true dots v_j^T a_c = a_jc + scale * sum u_i a_ic (v_j has a one on the
-// diagonal), the forward recurrence of T, and the update factors
-// tau * v_j^T a_c for the next pass.  One pass and one reduction per column
-// (Householder convention beta = -sign(alpha) |x|, sign(0) = +1).
-__device__ void panel_factor_mixed(float* Y, int64_t ldy, int64_t k, int nbk, int64_t h, double* tau_out,
-                                   double* sT, double* sred, double* sout, float* Pb) {
-  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  const int nwarps = nthr >> 5;
-  float* spart = (float*)sred;     // [warp][32][2] partial sums (s, c)
-  float* srow = (float*)sout;      // [32] row j of the panel
-  float* sfc = srow + kNB2;        // [32] tau * v_j^T a_c (zero outside (jj, nbk))
-  float* sscale = sfc + kNB2;      // [1]  scale of column jj
-  // gather: Pb[(i - k) * 32 + c] = Y[i, k + c] (zeros beyond nbk)
-  for (int64_t i = k + tid; i < h; i += nthr) {
-    float4* pr = (float4*)(Pb + (i - k) * kNB2);
+// ---------------------------------------------------------------------------
+// Panel factorisation: chunked TSQR + Householder reconstruction
+// ---------------------------------------------------------------------------
+// The panel A (L = h - k rows, nbk <= 32 columns) is too tall for the SM's
+// on-chip memory, so a column-by-column Householder sweep would stream it
+// once per column.  Instead (three passes over the panel):
+//   1. every 128-row chunk is factored by one warp in registers
+//      (Householder, lane = rows lane + 32 q), chunk R to scratch, the
+//      chunk's reflectors back into the panel;
+//   2. the chunk R factors are merged pairwise up a binary tree (a warp per
+//      merge, lane = column; a merge's reflectors replace the right child's
+//      R), then the explicit Q (L x nbk) of the panel is formed top-down:
+//      the root block I is pushed through the merges and every chunk's
+//      reflectors, and written over the panel;
+//   3. Householder reconstruction (Ballard et al., "Reconstructing
+//      Householder vectors from tall-skinny QR", 2015): with signs
+//      s_j = -sign of the pivot, the LU factorisation without pivoting
+//      Q - [S; 0] = V U gives the unit lower trapezoidal reflector matrix V,
+//      T = -U S V1^-T (upper triangular, tau_j = T_jj in [1, 2]) and
+//      R = S R_tsqr, so that (I - V T V^T)[R; 0] = A, the same compact WY
+//      form the column sweep produces.  V's rows below the top block are
+//      the rows of Q U^-1 (one pass, a thread per row).
+constexpr int kCR = 128;                                   // rows per chunk (4 per lane)
+constexpr int kHrSlot = 2 * kNB2 * kNB2 + 2 * kNB2;        // floats per chunk: R / node reflectors, Q block, taus
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float warp_sumf(float v) {
 #pragma unroll
-    for (int q = 0; q < kNB2 / 4; ++q) {
-      float4 v;
-      v.x = (4 * q + 0 < nbk) ? Y[i + (k + 4 * q + 0) * ldy] : 0.f;
-      v.y = (4 * q + 1 < nbk) ? Y[i + (k + 4 * q + 1) * ldy] : 0.f;
-      v.z = (4 * q + 2 < nbk) ? Y[i + (k + 4 * q + 2) * ldy] : 0.f;
-      v.w = (4 * q + 3 < nbk) ? Y[i + (k + 4 * q + 3) * ldy] : 0.f;
-      pr[q] = v;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Householder scalars for [alpha; x] with xx = |x|^2 (convention beta = -sign(alpha) |.|, sign(0) = +1)
+__device__ __forceinline__ void house_scalars(float alpha, float xx, float& tau, float& beta, float& scale) {
+  tau = 0.f;
+  beta = alpha;
+  scale = 0.f;
+  if (xx > 0.f) {
+    const float nrm = sqrtf(fmaf(alpha, alpha, xx));
+    beta = alpha >= 0.f ? -nrm : nrm;
+    tau = (beta - alpha) / beta;
+    scale = 1.f / (alpha - beta);
+  }
+}
+
+// Step 1: Householder QR of each 128-row chunk, one warp per chunk.
+__device__ void hr_chunks(float* Y, int64_t ldy, int64_t k, int nbk, int64_t L, int64_t nc, float* hs) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t c = warp; c < nc; c += nw) {
+    const int64_t base = k + c * kCR;
+    const int64_t nrow = (L - c * kCR) < kCR ? (L - c * kCR) : kCR;
+    float a[4][kNB2];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t row = lane + 32 * q;
+#pragma unroll
+      for (int col = 0; col < kNB2; ++col)
+        a[q][col] = (row < nrow && col < nbk) ? Y[base + row + (k + col) * ldy] : 0.f;
+    }
+    float mytau = 0.f;
+#pragma unroll
+    for (int j = 0; j < kNB2; ++j) {
+      if (j < nbk) {
+        float xx = (lane > j) ? a[0][j] * a[0][j] : 0.f;
+#pragma unroll
+        for (int q = 1; q < 4; ++q) xx = fmaf(a[q][j], a[q][j], xx);
+        xx = warp_sumf(xx);
+        const float alpha = __shfl_sync(kFull, a[0][j], j);
+        float tau, beta, scale;
+        house_scalars(alpha, xx, tau, beta, scale);
+        if (lane > j) a[0][j] *= scale;
+#pragma unroll
+        for (int q = 1; q < 4; ++q) a[q][j] *= scale;
+        if (lane == j) mytau = tau;
+#pragma unroll
+        for (int col = j + 1; col < kNB2; ++col) {
+          float d = (lane > j) ? a[0][j] * a[0][col] : 0.f;
+#pragma unroll
+          for (int q = 1; q < 4; ++q) d = fmaf(a[q][j], a[q][col], d);
+          d = (warp_sumf(d) + __shfl_sync(kFull, a[0][col], j)) * tau;
+          if (lane > j) a[0][col] = fmaf(-d, a[0][j], a[0][col]);
+#pragma unroll
+          for (int q = 1; q < 4; ++q) a[q][col] = fmaf(-d, a[q][j], a[q][col]);
+          if (lane == j) a[0][col] -= d;
+        }
+        if (lane == j) a[0][j] = beta;
+      }
+    }
+    float* Rc = hs + c * kHrSlot;
+#pragma unroll
+    for (int col = 0; col < kNB2; ++col) Rc[lane * kNB2 + col] = (col >= lane) ? a[0][col] : 0.f;
+    Rc[2 * kNB2 * kNB2 + lane] = mytau;   // chunk taus
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t row = lane + 32 * q;
+      if (row < nrow) {
+#pragma unroll
+        for (int col = 0; col < kNB2; ++col)
+          if (col < nbk) Y[base + row + (k + col) * ldy] = a[q][col];
+      }
     }
   }
-  if (tid < kNB2) sfc[tid] = 0.f;
-  if (tid == 0) sscale[0] = 0.f;
+}
+
+// Step 2a: merge the upper triangles Ra (left) and Rb (right): [Ra; Rb] =
+// H [R; 0]; R replaces Ra, the reflectors' lower parts (column j: rows
+// 0..j of the bottom half) replace Rb, their taus go to tn.  Lane = column.
+__device__ void hr_merge(float* Ra, float* Rb, float* tn, int nbk) {
+  const int lane = threadIdx.x & 31;
+  float ra[kNB2], rb[kNB2];
+#pragma unroll
+  for (int r = 0; r < kNB2; ++r) {
+    ra[r] = Ra[r * kNB2 + lane];
+    rb[r] = (r <= lane) ? Rb[r * kNB2 + lane] : 0.f;
+  }
+  float mytau = 0.f;
+#pragma unroll
+  for (int j = 0; j < kNB2; ++j) {
+    if (j < nbk) {
+      float xo = 0.f;
+#pragma unroll
+      for (int r = 0; r <= j; ++r) xo = fmaf(rb[r], rb[r], xo);
+      const float xx = __shfl_sync(kFull, xo, j);
+      const float alpha = __shfl_sync(kFull, ra[j], j);
+      float tau, beta, scale;
+      house_scalars(alpha, xx, tau, beta, scale);
+      float vb[kNB2];
+#pragma unroll
+      for (int r = 0; r <= j; ++r) vb[r] = __shfl_sync(kFull, rb[r], j) * scale;
+      if (lane > j) {
+        float d = ra[j];
+#pragma unroll
+        for (int r = 0; r <= j; ++r) d = fmaf(vb[r], rb[r], d);
+        d *= tau;
+        ra[j] -= d;
+#pragma unroll
+        for (int r = 0; r <= j; ++r) rb[r] = fmaf(-d, vb[r], rb[r]);
+      }
+      if (lane == j) {
+        ra[j] = beta;
+#pragma unroll
+        for (int r = 0; r <= j; ++r) rb[r] = vb[r];
+        mytau = tau;
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kNB2; ++r) {
+    Ra[r * kNB2 + lane] = ra[r];
+    Rb[r * kNB2 + lane] = rb[r];
+  }
+  tn[lane] = mytau;
+}
+
+// Step 2b: [Bi; Bj] = H [Bi; 0] for the merge whose reflectors sit in Vn
+// (H = H_0 ... H_{nbk-1}, applied last to first).  Lane = column.
+__device__ void hr_down(float* Bi, float* Bj, const float* Vn, const float* tn, int nbk) {
+  const int lane = threadIdx.x & 31;
+  float xt[kNB2], xb[kNB2];
+#pragma unroll
+  for (int r = 0; r < kNB2; ++r) {
+    xt[r] = Bi[r * kNB2 + lane];
+    xb[r] = 0.f;
+  }
+#pragma unroll
+  for (int j = kNB2 - 1; j >= 0; --j) {
+    if (j < nbk) {
+      const float tau = tn[j];
+      float vb[kNB2];
+#pragma unroll
+      for (int r = 0; r <= j; ++r) vb[r] = Vn[r * kNB2 + j];
+      float d = xt[j];
+#pragma unroll
+      for (int r = 0; r <= j; ++r) d = fmaf(vb[r], xb[r], d);
+      d *= tau;
+      xt[j] -= d;
+#pragma unroll
+      for (int r = 0; r <= j; ++r) xb[r] = fmaf(-d, vb[r], xb[r]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kNB2; ++r) {
+    Bi[r * kNB2 + lane] = xt[r];
+    Bj[r * kNB2 + lane] = xb[r];
+  }
+}
+
+// Step 2c: the chunk's rows of the explicit Q: H_chunk [B_c; 0], written
+// over the chunk's reflectors.  Lane = rows lane + 32 q.
+__device__ void hr_chunk_q(float* Y, int64_t ldy, int64_t k, int nbk, int64_t L, int64_t c, const float* hs) {
+  const int lane = threadIdx.x & 31;
+  const int64_t base = k + c * kCR;
+  const int64_t nrow = (L - c * kCR) < kCR ? (L - c * kCR) : kCR;
+  const float* Bc = hs + c * kHrSlot + kNB2 * kNB2;
+  const float* tch = hs + c * kHrSlot + 2 * kNB2 * kNB2;
+  float x[4][kNB2];
+#pragma unroll
+  for (int col = 0; col < kNB2; ++col) {
+    x[0][col] = Bc[lane * kNB2 + col];
+    x[1][col] = x[2][col] = x[3][col] = 0.f;
+  }
+#pragma unroll 1
+  for (int j = nbk - 1; j >= 0; --j) {
+    float v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t row = lane + 32 * q;
+      v[q] = (row == j) ? 1.f : ((row > j && row < nrow) ? Y[base + row + (k + j) * ldy] : 0.f);
+    }
+    const float tau = tch[j];
+#pragma unroll
+    for (int col = 0; col < kNB2; ++col) {
+      float d = v[0] * x[0][col];
+#pragma unroll
+      for (int q = 1; q < 4; ++q) d = fmaf(v[q], x[q][col], d);
+      d = warp_sumf(d) * tau;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) x[q][col] = fmaf(-d, v[q], x[q][col]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t row = lane + 32 * q;
+    if (row < nrow) {
+#pragma unroll
+      for (int col = 0; col < kNB2; ++col)
+        if (col < nbk) Y[base + row + (k + col) * ldy] = x[q][col];
+    }
+  }
+}
+
+// The panel [k, k + nbk) of the leaf (rows k .. h-1): reflectors below the
+// diagonal, R on and above it, T (FP64, row-major) in sT, taus in tau_out.
+// sf: >= 33 * 32 * 2 + 64 floats of shared memory; hs: the leaf's scratch
+// (ceil((h - k) / 128) chunk slots).
+__device__ void panel_tsqr_hr(float* Y, int64_t ldy, int64_t k, int nbk, int64_t h, double* tau_out, double* sT,
+                              float* sf, float* hs) {
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+  const int64_t L = h - k;
+  const int64_t nc = (L + kCR - 1) / kCR;
+  hr_chunks(Y, ldy, k, nbk, L, nc, hs);
   __syncthreads();
-  for (int jj = 0; jj < nbk; ++jj) {
-    const int64_t j = k + jj;
-    float fc[kNB2];
-#pragma unroll
-    for (int c = 0; c < kNB2; ++c) fc[c] = sfc[c];
-    const float scp = sscale[0];
-    KSum32 acc[kNB2];   // acc[jj] collects sum u_i^2
-    for (int64_t i = (jj > 0 ? j - 1 : j) + tid; i < h; i += nthr) {
-      float4* pr = (float4*)(Pb + (i - k) * kNB2);
-      float row[kNB2];
-#pragma unroll
-      for (int q = 0; q < kNB2 / 4; ++q) {
-        const float4 v4 = pr[q];
-        row[4 * q] = v4.x; row[4 * q + 1] = v4.y; row[4 * q + 2] = v4.z; row[4 * q + 3] = v4.w;
-      }
-      if (jj > 0) {
-        // row[jj - 1] re-read from the (L1-resident) row rather than indexed
-        // at run time, which would move row[] out of registers
-        const float rp = ((const float*)pr)[jj - 1];
-        const float v = (i == j - 1) ? 1.f : rp * scp;
-        // fc is zero outside (jj - 1, nbk), so the update needs no column test
-#pragma unroll
-        for (int c = 0; c < kNB2; ++c) row[c] = (c == jj - 1) ? (i > j - 1 ? v : row[c]) : row[c] - fc[c] * v;
-      }
-      if (i == j) {
-#pragma unroll
-        for (int c = 0; c < kNB2; ++c) srow[c] = row[c];
-      } else if (i > j) {
-        float u = 0.f;
-#pragma unroll
-        for (int c = 0; c < kNB2; ++c) u = (c == jj) ? row[c] : u;
-#pragma unroll
-        for (int c = 0; c < kNB2; ++c)
-          if (c < nbk) acc[c].add(u * row[c]);
-      }
-      if (jj > 0) {
-#pragma unroll
-        for (int q = 0; q < kNB2 / 4; ++q)
-          pr[q] = make_float4(row[4 * q], row[4 * q + 1], row[4 * q + 2], row[4 * q + 3]);
-      }
-    }
-    // block reduction of the 32 compensated sums: TwoSum shuffles, then the
-    // warps' partials in FP64 by warp 0 (lane c owns value c)
-#pragma unroll
-    for (int c = 0; c < kNB2; ++c) {
-      F2 v{acc[c].s, -acc[c].c};
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        F2 w{__shfl_xor_sync(0xffffffffu, v.s, o), __shfl_xor_sync(0xffffffffu, v.c, o)};
-        v = f2_add(v, w);
-      }
-      if (lane == 0) {
-        spart[(warp * kNB2 + c) * 2] = v.s;
-        spart[(warp * kNB2 + c) * 2 + 1] = v.c;
-      }
-    }
+  int64_t top = 0;
+  for (int64_t st = 1; st < nc; st *= 2) {
+    for (int64_t i = (int64_t)warp * 2 * st; i < nc; i += (int64_t)nw * 2 * st)
+      if (i + st < nc) hr_merge(hs + i * kHrSlot, hs + (i + st) * kHrSlot, hs + (i + st) * kHrSlot + 2 * kNB2 * kNB2 + kNB2, nbk);
+    top = st;
     __syncthreads();
-    if (warp == 0) {
-      const int c = lane;
-      double tot = 0.0;
-      for (int w = 0; w < nwarps; ++w)
-        tot += (double)spart[(w * kNB2 + c) * 2] + (double)spart[(w * kNB2 + c) * 2 + 1];
-      const double xx = __shfl_sync(0xffffffffu, tot, jj);
-      double tau_j = 0.0, beta = 0.0, scale = 0.0;
-      if (lane == 0) {
-        const double alpha = (double)srow[jj];
-        beta = alpha;
-        if (xx != 0.0) {
-          const double nrm = sqrt(alpha * alpha + xx);
-          beta = (alpha >= 0.0) ? -nrm : nrm;
-          tau_j = (beta - alpha) / beta;
-          scale = 1.0 / (alpha - beta);
+  }
+  // root R (row-major) to shared memory before the Q blocks overwrite nothing of it
+  float* sU = sf;                      // 32 x 33: U of the LU, then reused
+  float* sR = sf + 32 * 33;            // 32 x 33: root R
+  float* sS = sR + 32 * 33;            // 32 signs
+  for (int idx = tid; idx < kNB2 * kNB2; idx += nthr) sR[(idx / kNB2) * 33 + idx % kNB2] = hs[idx];
+  // B_0 = I
+  for (int idx = tid; idx < kNB2 * kNB2; idx += nthr)
+    hs[kNB2 * kNB2 + idx] = (idx / kNB2 == idx % kNB2 && idx % kNB2 < nbk) ? 1.f : 0.f;
+  __syncthreads();
+  for (int64_t st = top; st >= 1; st /= 2) {
+    for (int64_t i = (int64_t)warp * 2 * st; i < nc; i += (int64_t)nw * 2 * st)
+      if (i + st < nc)
+        hr_down(hs + i * kHrSlot + kNB2 * kNB2, hs + (i + st) * kHrSlot + kNB2 * kNB2, hs + (i + st) * kHrSlot,
+                hs + (i + st) * kHrSlot + 2 * kNB2 * kNB2 + kNB2, nbk);
+    __syncthreads();
+  }
+  for (int64_t c = warp; c < nc; c += nw) hr_chunk_q(Y, ldy, k, nbk, L, c, hs);
+  __syncthreads();
+  // modified LU of the top block Q1 - S (warp 0, lane = column)
+  if (warp == 0) {
+    float q[kNB2];
+#pragma unroll
+    for (int r = 0; r < kNB2; ++r) q[r] = (r < nbk && lane < nbk) ? Y[k + r + (k + lane) * ldy] : 0.f;
+#pragma unroll
+    for (int j = 0; j < kNB2; ++j) {
+      if (j < nbk) {
+        const float pj = __shfl_sync(kFull, q[j], j);
+        const float sj = pj >= 0.f ? -1.f : 1.f;
+        const float u = pj - sj;                     // |u| >= 1
+        if (lane == j) {
+          q[j] = u;
+#pragma unroll
+          for (int r = j + 1; r < kNB2; ++r) q[r] /= u;
+        }
+        if (lane == 0) sS[j] = sj;
+        float l[kNB2];
+#pragma unroll
+        for (int r = j + 1; r < kNB2; ++r) l[r] = __shfl_sync(kFull, q[r], j);
+        if (lane > j) {
+#pragma unroll
+          for (int r = j + 1; r < kNB2; ++r) q[r] = fmaf(-l[r], q[j], q[r]);
         }
       }
-      tau_j = __shfl_sync(0xffffffffu, tau_j, 0);
-      scale = __shfl_sync(0xffffffffu, scale, 0);
-      // w_c = v_j^T a_c (c > jj) or v_c^T v_j (c < jj)
-      const double wcv = (c < nbk && c != jj) ? (double)srow[c] + scale * tot : 0.0;
-      // T[0:jj, jj] = -tau T[0:jj, 0:jj] w[0:jj]; lane p owns row p
-      double tp = 0.0;
-      for (int q = 0; q < jj; ++q) {
-        const double wq = __shfl_sync(0xffffffffu, wcv, q);
-        if (c <= q) tp += sT[c * kNB2 + q] * wq;
-      }
-      if (c < jj) sT[c * kNB2 + jj] = -tau_j * tp;
-      if (c == jj) {
-        sT[jj * kNB2 + jj] = tau_j;
-        tau_out[jj] = tau_j;
-      }
-      sfc[c] = (c > jj && c < nbk) ? (float)(tau_j * wcv) : 0.f;
-      if (lane == 0) {
-        sscale[0] = (float)scale;
-        Pb[(j - k) * kNB2 + jj] = (float)beta;
-      }
     }
-    __syncthreads();
-  }
-  // scatter the factored panel back; the last column's sub-diagonal still
-  // needs its scale
-  const float scl = sscale[0];
-  for (int64_t i = k + tid; i < h; i += nthr) {
-    const float4* pr = (const float4*)(Pb + (i - k) * kNB2);
 #pragma unroll
-    for (int q = 0; q < kNB2 / 4; ++q) {
-      const float4 v = pr[q];
-#define PYLOM_SCATTER_ONE(t, e)                                                   \
-  {                                                                               \
-    const int c = 4 * q + (t);                                                    \
-    if (c < nbk) Y[i + (k + c) * ldy] = (c == nbk - 1 && i > k + c) ? (e) * scl : (e); \
+    for (int r = 0; r < kNB2; ++r) sU[r * 33 + lane] = q[r];   // U on and above the diagonal, L1 below
   }
-      PYLOM_SCATTER_ONE(0, v.x)
-      PYLOM_SCATTER_ONE(1, v.y)
-      PYLOM_SCATTER_ONE(2, v.z)
-      PYLOM_SCATTER_ONE(3, v.w)
-#undef PYLOM_SCATTER_ONE
+  __syncthreads();
+  // V rows below the top block: y = x U^-1 (a thread per row)
+  for (int64_t i = k + nbk + tid; i < h; i += nthr) {
+    float y[kNB2];
+#pragma unroll
+    for (int col = 0; col < kNB2; ++col) y[col] = (col < nbk) ? Y[i + (k + col) * ldy] : 0.f;
+#pragma unroll
+    for (int j = 0; j < kNB2; ++j) {
+      if (j < nbk) {
+        float acc = y[j];
+#pragma unroll
+        for (int l = 0; l < j; ++l) acc = fmaf(-y[l], sU[l * 33 + j], acc);
+        y[j] = acc / sU[j * 33 + j];
+      }
     }
+#pragma unroll
+    for (int col = 0; col < kNB2; ++col)
+      if (col < nbk) Y[i + (k + col) * ldy] = y[col];
+  }
+  // top block: V1 strictly below the diagonal, R = S R_tsqr on and above it
+  for (int idx = tid; idx < nbk * nbk; idx += nthr) {
+    const int r = idx % nbk, col = idx / nbk;
+    Y[k + r + (k + col) * ldy] = (r > col) ? sU[r * 33 + col] : sS[r] * sR[r * 33 + col];
+  }
+  // T = -U S V1^-T in FP64 (warp 0, lane = column): Z = V1^-T by back
+  // substitution of V1^T Z = I, then T[p][c] = -sum_m U[p][m] s_m Z[m][c]
+  if (warp == 0) {
+    double z[kNB2];
+#pragma unroll
+    for (int r = kNB2 - 1; r >= 0; --r) {
+      double acc = (r == lane) ? 1.0 : 0.0;
+#pragma unroll
+      for (int m = r + 1; m < kNB2; ++m) acc -= (double)sU[m * 33 + r] * z[m];   // V1[m][r]
+      z[r] = (r <= lane && r < nbk && lane < nbk) ? acc : 0.0;
+    }
+#pragma unroll
+    for (int p = 0; p < kNB2; ++p) {
+      double acc = 0.0;
+#pragma unroll
+      for (int m = p; m < kNB2; ++m) acc += (double)sU[p * 33 + m] * (double)sS[m] * z[m];
+      sT[p * kNB2 + lane] = (p <= lane && lane < nbk) ? -acc : 0.0;
+    }
+    if (lane < nbk) tau_out[lane] = -(double)sU[lane * 33 + lane] * (double)sS[lane];
   }
   __syncthreads();
 }
@@ -474,10 +659,18 @@ __device__ void mixed_prologue(const MixedArgs& a, float* Y, int64_t ldy, int64_
   int bad = 0;
   for (int64_t i = threadIdx.x; i < h; i += blockDim.x) {
     const int64_t n = r0 + i;
+    // kPro independent loads in flight per thread (one 8-warp CTA per SM)
+    constexpr int kPro = 16;
     double xbar = 0.0;
     if (a.remove_mean) {
       double sum = 0.0;
-      for (int64_t m = 0; m < M; ++m) sum += (double)X[n + m * a.ldx];
+      for (int64_t m0 = 0; m0 < M; m0 += kPro) {
+        double xv[kPro];
+#pragma unroll
+        for (int u = 0; u < kPro; ++u) xv[u] = (m0 + u < M) ? (double)X[n + (m0 + u) * a.ldx] : 0.0;
+#pragma unroll
+        for (int u = 0; u < kPro; ++u) sum += xv[u];
+      }
       xbar = sum / (double)M;
     }
     if (a.mean) a.mean[n] = xbar;
@@ -487,10 +680,17 @@ __device__ void mixed_prologue(const MixedArgs& a, float* Y, int64_t ldy, int64_
       if (!(wn > 0.0) || !isfinite(wn)) bad = 1;
       sw = sqrt(wn);
     }
-    for (int64_t m = 0; m < M; ++m) {
-      const double x = (double)X[n + m * a.ldx];
-      if (!isfinite(x)) bad = 1;
-      Y[i + m * ldy] = (float)(sw * (x - xbar));
+    for (int64_t m0 = 0; m0 < M; m0 += kPro) {
+      double xv[kPro];
+#pragma unroll
+      for (int u = 0; u < kPro; ++u) xv[u] = (m0 + u < M) ? (double)X[n + (m0 + u) * a.ldx] : 0.0;
+#pragma unroll
+      for (int u = 0; u < kPro; ++u) {
+        if (m0 + u < M) {
+          if (!isfinite(xv[u])) bad = 1;
+          Y[i + (m0 + u) * ldy] = (float)(sw * (xv[u] - xbar));
+        }
+      }
     }
   }
   if (bad) raise_status(a.s.hdr, PYLOM_ERR_NONFINITE);
@@ -527,7 +727,7 @@ __global__ void __launch_bounds__(kMxThreads) leaf_qr_mixed_kernel(MixedArgs a) 
     const int nbk = (int)((M - k) < kNB2 ? (M - k) : kNB2);
     for (int idx = tid; idx < kNB2 * kNB2; idx += blockDim.x) sT[idx] = 0.0;
     __syncthreads();
-    panel_factor_mixed(Y, ldy, k, nbk, h, s.tau + leaf * M + k, sT, sred, sout, a.Pb + r0 * kNB2);
+    panel_tsqr_hr(Y, ldy, k, nbk, h, s.tau + leaf * M + k, sT, (float*)msm, a.Pb + (r0 / kCR + leaf) * kHrSlot);
     __syncthreads();
     double* Tg = a.T2 + (leaf * npan + k / kNB2) * kNB2 * kNB2;
     for (int idx = tid; idx < kNB2 * kNB2; idx += blockDim.x) Tg[idx] = sT[idx];
@@ -665,7 +865,7 @@ __global__ void __launch_bounds__(kMxThreads) leaf_qt_mixed_kernel(TsqrState s, 
 size_t mixed_extra_bytes(int64_t N, int64_t M, int64_t P) {
   const int64_t npan = (M + kNB2 - 1) / kNB2;
   return align256(sizeof(float) * (size_t)N * M) + align256(sizeof(double) * (size_t)P * npan * kNB2 * kNB2) +
-         align256(sizeof(float) * (size_t)N * kNB2);
+         align256(sizeof(float) * (size_t)(N / kCR + P + 1) * kHrSlot);
 }
 
 cudaError_t launch_tsqr_mixed(const TsqrState& s, char* extra, const void* X, int64_t ldx, int xtype,
