@@ -686,18 +686,33 @@ def run_ours(args, rank, world, local_rank):
         rh = torch.empty(1, dtype=torch.int64, pin_memory=True)
         d2h = 0
 
-        def e2e_step():
+        split = {"h2d": 0.0, "pod": 0.0, "d2h": 0.0}
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+        def e2e_step(record=False):
             nonlocal d2h
+            if record:
+                ev[0].record()
             Xd.copy_(Xh, non_blocking=True)
             wd.copy_(wh, non_blocking=True)
+            if record:
+                ev[1].record()
             pg.pod(Xd.t(), w=wd, remove_mean=False, energy=ENERGY, r_max=M, leaf_rows=args.leaf_rows,
                    workspace=ws, out=out, check=False)
+            if record:
+                ev[2].record()
             rh.copy_(r_dev, non_blocking=True)
             Sh.copy_(S, non_blocking=True)
             VTh.copy_(VT.t(), non_blocking=True)
             torch.cuda.current_stream().synchronize()
             rr = int(rh.item())
             Uh[:rr].copy_(U.t()[:rr], non_blocking=True)
+            if record:
+                ev[3].record()
+                ev[3].synchronize()
+                split["h2d"] += ev[0].elapsed_time(ev[1])
+                split["pod"] += ev[1].elapsed_time(ev[2])
+                split["d2h"] += ev[2].elapsed_time(ev[3])
             d2h = 8 + M * 8 + M * M * 8 + rr * N * 8
         e2e_step()
         torch.cuda.synchronize()
@@ -715,8 +730,12 @@ def run_ours(args, rank, world, local_rank):
             t = torch.tensor([ems], dtype=torch.float64, device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ems = float(t.item())
+        # one more step with events between its parts (outside the timed region)
+        e2e_step(record=True)
+        torch.cuda.synchronize()
         e2e = {"value": world * bytes_x / (ems * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ems,
-               "h2d_bytes_per_step": N * M * 8 + N * 8, "d2h_bytes_per_step": d2h}
+               "h2d_bytes_per_step": N * M * 8 + N * 8, "d2h_bytes_per_step": d2h,
+               "split_ms_one_step": split}
         del Xh, Uh
 
     cpu = None
