@@ -735,7 +735,8 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         e2e = {"value": world * bytes_x / (ems * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ems,
                "h2d_bytes_per_step": N * M * 8 + N * 8, "d2h_bytes_per_step": d2h,
-               "split_ms_one_step": split}
+               "split_ms_one_step": split, "host_buffers_pinned": bool(Xh.is_pinned() and Uh.is_pinned()),
+               "h2d_gbs_one_step": (N * M * 8 + N * 8) / (split["h2d"] * 1e-3) / 1e9 if split["h2d"] > 0 else None}
         del Xh, Uh
 
     cpu = None
