@@ -94,6 +94,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def rank_max(value: float, device=None) -> float:
+    """Max of a per-rank time over the job's ranks (the slowest rank sets the
+    step time); the value itself on a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gbs(bytes_per_rank: float, ms: float, world: int) -> float:
+    """Whole-job throughput: every rank processes its own bytes_per_rank in ms."""
+    return world * bytes_per_rank / (ms * 1e-3) / 1e9
+
+
 def cpu_baseline(n_rows: int, M: int, seed_shift: int = 0):
     """The FP64 oracle, as it stands, on a row sample of the workload.
     Returns (GB/s of X, seconds, threads, sample description)."""
@@ -650,13 +667,9 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     phases, ncalls = pg.profile_end()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = rank_max(e0.elapsed_time(e1) / args.steps, dev)
     bytes_x = N * M * 8
-    value = world * bytes_x / (ms * 1e-3) / 1e9
+    value = job_gbs(bytes_x, ms, world)
 
     # dominant kernel: leaf QR + tree (one launch per step)
     leaf_ms = phases["leaf_qr_tree"] / max(ncalls, 1)
@@ -725,15 +738,11 @@ def run_ours(args, rank, world, local_rank):
             e2e_step()
         f1.record()
         torch.cuda.synchronize()
-        ems = f0.elapsed_time(f1) / args.steps
-        if world > 1:
-            t = torch.tensor([ems], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = rank_max(f0.elapsed_time(f1) / args.steps, dev)
         # one more step with events between its parts (outside the timed region)
         e2e_step(record=True)
         torch.cuda.synchronize()
-        e2e = {"value": world * bytes_x / (ems * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ems,
+        e2e = {"value": job_gbs(bytes_x, ems, world), "unit": "GB/s", "ms_per_step": ems,
                "h2d_bytes_per_step": N * M * 8 + N * 8, "d2h_bytes_per_step": d2h,
                "split_ms_one_step": split, "host_buffers_pinned": bool(Xh.is_pinned() and Uh.is_pinned()),
                "h2d_gbs_one_step": (N * M * 8 + N * 8) / (split["h2d"] * 1e-3) / 1e9 if split["h2d"] > 0 else None}
