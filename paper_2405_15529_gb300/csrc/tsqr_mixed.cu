@@ -493,36 +493,44 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
 #pragma unroll
     for (int p = 0; p < 16; ++p) ws_[p] = wc_[p] = 0.f;
     const int64_t nkc = (L + kKC - 1) / kKC;
-    // loads: thread t takes row t % 64 of the step and columns (reflectors)
-    // t / 64 + 4 u; consecutive lanes read consecutive rows
-    const int lr = tid & (kKC - 1), lg = tid / kKC;
+    // staging map: warp instruction u of warp w covers core matrix u * 8 + w
+    // of the operand (8 operand rows x 4 K elements, 128 contiguous bytes of
+    // shared memory), so the split stores are free of bank conflicts; lane l
+    // holds operand row 8 g + l / 4 and K element 4 q + l % 4 of it
+    const int lrow = lane >> 2, lk = lane & 3;
     float xa[kCH / 4], xb[kNB2 / 4];
     auto load_w = [&](int64_t kc) {
-      const int64_t row = k + kc * kKC + lr;
-      const bool rok = row < h;
 #pragma unroll
-      for (int u = 0; u < kCH / 4; ++u) {
-        const int c = lg + 4 * u;
-        xa[u] = (rok && c < wc) ? C[row + (int64_t)(c0 + c) * ldc] : 0.f;
+      for (int u = 0; u < kCH / 4; ++u) {          // A: 16 row groups x 16 K groups
+        const int cmi = u * 8 + warp;
+        const int c = (cmi & 15) * 8 + lrow;
+        const int64_t row = k + kc * kKC + (cmi >> 4) * 4 + lk;
+        xa[u] = (row < h && c < wc) ? C[row + (int64_t)(c0 + c) * ldc] : 0.f;
       }
 #pragma unroll
-      for (int u = 0; u < kNB2 / 4; ++u) xb[u] = vval_f(Y, ldy, k, nbk, h, row, lg + 4 * u);
+      for (int u = 0; u < kNB2 / 4; ++u) {         // B: 4 reflector groups x 16 K groups
+        const int cmi = u * 8 + warp;
+        const int64_t row = k + kc * kKC + (cmi >> 2) * 4 + lk;
+        xb[u] = vval_f(Y, ldy, k, nbk, h, row, (cmi & 3) * 8 + lrow);
+      }
     };
     load_w(0);
     for (int64_t kc = 0; kc < nkc && ok; ++kc) {
 #pragma unroll
       for (int u = 0; u < kCH / 4; ++u) {
+        const int cmi = u * 8 + warp;
         float hi, lo;
         split_tf32(xa[u], hi, lo);
-        const uint32_t o = cm_off(lg + 4 * u, lr, kKC);
+        const uint32_t o = cm_off((cmi & 15) * 8 + lrow, (cmi >> 4) * 4 + lk, kKC);
         *(float*)(smem + kOffWA + o) = hi;
         *(float*)(smem + kOffWAlo + o) = lo;
       }
 #pragma unroll
       for (int u = 0; u < kNB2 / 4; ++u) {
+        const int cmi = u * 8 + warp;
         float hi, lo;
         split_tf32(xb[u], hi, lo);
-        const uint32_t o = cm_off(lg + 4 * u, lr, kKC);
+        const uint32_t o = cm_off((cmi & 3) * 8 + lrow, (cmi >> 2) * 4 + lk, kKC);
         *(float*)(smem + kOffWB + o) = hi;
         *(float*)(smem + kOffWBlo + o) = lo;
       }
@@ -581,6 +589,8 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
     }
     // ---- C stage: per 256-row tile, P = V_tile W' (two 128-row MMAs); C += P ----
     const int64_t nrt = (L + kRT - 1) / kRT;
+    // V tile: thread t stages row t of the tile (whole 128-byte reflector
+    // rows from global memory; a core-matrix-ordered map was slower here)
     float xv[kNB2];
     auto load_v = [&](int64_t rt) {
       const int64_t row = k + rt * kRT + tid;
