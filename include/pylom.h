@@ -47,7 +47,7 @@ typedef enum {
   PYLOM_ERR_NONFINITE = 5,   /* device: the input holds NaN or Inf */
   PYLOM_ERR_NOCONV = 6,      /* device: Jacobi SVD hit max_sweeps */
   PYLOM_ERR_TIMEOUT = 7,     /* device: a bounded inter-block wait ran out */
-  PYLOM_ERR_UNSUPPORTED = 8, /* valid request this build does not implement */
+  PYLOM_ERR_UNSUPPORTED = 8, /* valid request the library does not implement */
   PYLOM_ERR_SINGULAR = 9     /* device: a matrix that must be positive definite is not (DMD amplitudes) */
 } pylom_status;
 

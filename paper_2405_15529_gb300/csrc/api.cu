@@ -317,7 +317,7 @@ extern "C" pylom_status pylom_tsqr(const void* A, int64_t N, int64_t M, int64_t 
   if (lda < N || ldr < M || (Q && ldq < N))
     return fail(PYLOM_ERR_ARG, "pylom_tsqr: leading dimension too small");
   if (prec != PYLOM_PREC_FP64)
-    return fail(PYLOM_ERR_UNSUPPORTED, "pylom_tsqr: this build implements PYLOM_PREC_FP64 only");
+    return fail(PYLOM_ERR_UNSUPPORTED, "pylom_tsqr: the library implements PYLOM_PREC_FP64 only here");
   const int64_t P = leaves_of(N, M, leaf_rows);
   const size_t need = tsqr_bytes(N, M, P, Q != nullptr);
   if (!aligned256(ws) || ws_bytes < need)
