@@ -138,6 +138,24 @@ __device__ __forceinline__ float warp_sumf(float v) {
   return v;
 }
 
+// Warp transpose-reduction: lane l ends with the sum over the warp of p[l]
+// (31 shuffles in five stages of independent exchanges, instead of one
+// five-step reduction per entry).  p is clobbered.
+__device__ __forceinline__ float reduce_scatter32(float (&p)[kNB2]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool hi = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const float send = hi ? p[i] : p[i + o];
+      const float keep = hi ? p[i + o] : p[i];
+      p[i] = keep + __shfl_xor_sync(kFull, send, o);
+    }
+  }
+  return p[0];
+}
+
 // Householder scalars for [alpha; x] with xx = |x|^2 (convention beta = -sign(alpha) |.|, sign(0) = +1)
 __device__ __forceinline__ void house_scalars(float alpha, float xx, float& tau, float& beta, float& scale) {
   tau = 0.f;
@@ -180,16 +198,26 @@ __device__ void hr_chunks(float* Y, int64_t ldy, int64_t k, int nbk, int64_t L, 
 #pragma unroll
         for (int q = 1; q < 4; ++q) a[q][j] *= scale;
         if (lane == j) mytau = tau;
+        // v's entry in this lane's first row: the reflector below the
+        // diagonal, its unit diagonal, zeros above
+        const float v0 = (lane > j) ? a[0][j] : (lane == j ? 1.f : 0.f);
+        if (j + 1 < kNB2) {
+          float pd[kNB2];
 #pragma unroll
-        for (int col = j + 1; col < kNB2; ++col) {
-          float d = (lane > j) ? a[0][j] * a[0][col] : 0.f;
+          for (int col = 0; col < kNB2; ++col) {
+            float d = (col > j) ? v0 * a[0][col] : 0.f;
 #pragma unroll
-          for (int q = 1; q < 4; ++q) d = fmaf(a[q][j], a[q][col], d);
-          d = (warp_sumf(d) + __shfl_sync(kFull, a[0][col], j)) * tau;
-          if (lane > j) a[0][col] = fmaf(-d, a[0][j], a[0][col]);
+            for (int q = 1; q < 4; ++q) d = (col > j) ? fmaf(a[q][j], a[q][col], d) : 0.f;
+            pd[col] = d;
+          }
+          const float mine = reduce_scatter32(pd) * tau;   // tau v^T a_col for col = lane
 #pragma unroll
-          for (int q = 1; q < 4; ++q) a[q][col] = fmaf(-d, a[q][j], a[q][col]);
-          if (lane == j) a[0][col] -= d;
+          for (int col = j + 1; col < kNB2; ++col) {
+            const float d = __shfl_sync(kFull, mine, col);
+            a[0][col] = fmaf(-d, v0, a[0][col]);
+#pragma unroll
+            for (int q = 1; q < 4; ++q) a[q][col] = fmaf(-d, a[q][j], a[q][col]);
+          }
         }
         if (lane == j) a[0][j] = beta;
       }
@@ -316,12 +344,18 @@ __device__ void hr_chunk_q(float* Y, int64_t ldy, int64_t k, int nbk, int64_t L,
       v[q] = (row == j) ? 1.f : ((row > j && row < nrow) ? Y[base + row + (k + j) * ldy] : 0.f);
     }
     const float tau = tch[j];
+    float pd[kNB2];
 #pragma unroll
     for (int col = 0; col < kNB2; ++col) {
       float d = v[0] * x[0][col];
 #pragma unroll
       for (int q = 1; q < 4; ++q) d = fmaf(v[q], x[q][col], d);
-      d = warp_sumf(d) * tau;
+      pd[col] = d;
+    }
+    const float mine = reduce_scatter32(pd) * tau;   // tau v^T x_col for col = lane
+#pragma unroll
+    for (int col = 0; col < kNB2; ++col) {
+      const float d = __shfl_sync(kFull, mine, col);
 #pragma unroll
       for (int q = 0; q < 4; ++q) x[q][col] = fmaf(-d, v[q], x[q][col]);
     }
