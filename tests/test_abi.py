@@ -104,3 +104,47 @@ def test_no_cpu_fallback():
         pytest.skip("GPU present")
     with pytest.raises(RuntimeError, match="no CUDA device"):
         pg.pod(torch.zeros(100, 10, dtype=torch.float64))
+
+
+def test_streamed_dmd_spod_host_queries(lib):
+    # streamed POD: the leaf height rule and the workspace query
+    assert pg.pod_streamed_leaf_rows(1 << 22, 256, 0, 1 << 20) == max(256, 1024, (1 << 20) // 304)
+    assert pg.pod_streamed_leaf_rows(1 << 22, 256, 2000, 1 << 20) == 2000
+    assert pg.pod_streamed_leaf_rows(1 << 22, 256, 100, 1 << 20) == -1      # leaves shorter than M
+    assert pg.pod_streamed_leaf_rows(1 << 22, 256, 0, 0) == -1               # no chunk
+    small = lib.pylom_pod_streamed_workspace_size(1 << 22, 256, 0, 1 << 18, 256, pg.F64)
+    large = lib.pylom_pod_streamed_workspace_size(1 << 22, 256, 0, 1 << 20, 256, pg.F64)
+    assert 0 < small < large
+    assert lib.pylom_pod_streamed_workspace_size(1 << 22, 256, 0, 1 << 20, 257, pg.F64) == 0
+    # DMD: M >= 2, 1 <= r_max <= M - 1
+    assert pg.dmd_workspace_size(10000, 64, 0, 63) > 10000 * 64 * 8
+    assert pg.dmd_workspace_size(10000, 64, 0, 64) == 0
+    assert pg.dmd_workspace_size(10000, 1, 0, 1) == 0
+    # SPOD front end: block and frequency counts of Alg. 6, as the oracle states them
+    from oracle import spod as osp
+    for T, npwin, nolap in [(4128, 64, 32), (100, 60, 30), (64, 64, 0), (301, 15, 5)]:
+        nb, nf = ctypes.c_int64(0), ctypes.c_int64(0)
+        assert lib.pylom_spod_shape(T, npwin, nolap, ctypes.byref(nb), ctypes.byref(nf)) == pg.OK
+        assert (nb.value, nf.value) == osp.spod_shape(T, npwin, nolap)
+    nb, nf = ctypes.c_int64(0), ctypes.c_int64(0)
+    assert lib.pylom_spod_shape(10, 32, 0, ctypes.byref(nb), ctypes.byref(nf)) == pg.ERR_SHAPE   # T < npwin
+
+
+def test_dmd_and_streamed_host_validation(lib):
+    fake = _vp(0x100000)  # never dereferenced: validation fails first
+    i64 = ctypes.c_int64(0)
+    st = lib.pylom_dmd(None, 1000, 20, 1000, pg.F64, 1, 0.0, 10, 0, fake, fake, fake, 1000, fake, None, fake,
+                       fake, 1 << 30, None)
+    assert st == pg.ERR_ARG
+    st = lib.pylom_dmd(fake, 1000, 1, 1000, pg.F64, 1, 0.0, 1, 0, fake, fake, fake, 1000, fake, None, fake,
+                       fake, 1 << 30, None)
+    assert st == pg.ERR_SHAPE                     # one snapshot
+    st = lib.pylom_dmd(fake, 1000, 20, 1000, pg.F64, 1, 0.0, 20, 0, fake, fake, fake, 1000, fake, None, fake,
+                       fake, 1 << 30, None)
+    assert st == pg.ERR_SHAPE                     # r_max > M - 1
+    st = lib.pylom_pod_streamed(fake, 1000, 20, 1000, pg.F64, None, 1, 0.0, 20, 0, 0, 0, fake, fake, 1000,
+                                fake, fake, 20, None, ctypes.byref(i64), fake, 1 << 30, None)
+    assert st == pg.ERR_SHAPE                     # chunk_rows = 0
+    st = lib.pylom_pod_streamed(fake, 1000, 20, 1000, pg.F64, None, 1, 0.0, 20, 0, 0, 1000, None, fake, 1000,
+                                fake, fake, 20, None, ctypes.byref(i64), fake, 1 << 30, None)
+    assert st == pg.ERR_ARG                       # no host scratch
