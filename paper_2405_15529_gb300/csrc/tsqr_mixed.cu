@@ -1,8 +1,8 @@
 // tsqr_mixed.cu -- mixed-precision leaves of the POD path (pyLOM, arXiv
 // 2405.15529, Alg. 1 / Eqs. svdqr1 and svdqr3) on the 5th-generation tensor
 // cores of GB300: FP32 working copy, Householder panels of kNB2 = 32
-// columns factored with compensated FP32 sums reduced in FP64 (FP64 scalars
-// tau, beta and T), and the block-reflector products on tcgen05 in 3xTF32
+// columns factored by chunked TSQR and Householder reconstruction (T in
+// FP64), and the block-reflector products on tcgen05 in 3xTF32
 // (x = hi + lo, hi exact in TF32; hi*hi + hi*lo + lo*hi accumulated in FP32
 // in tensor memory).  The tree, the small SVD and the top-down pass stay in
 // binary64 (they are the FP64 path's kernels).
@@ -50,9 +50,7 @@ constexpr int kOpBytes = 6 * kCA;                  // 96 KB >= the W stage's 80 
 static_assert(2 * kWA + 2 * kWB <= kOpBytes, "W-stage operands must fit the operand region");
 constexpr int kOffW = kOpBytes;                    // W: 32 x 128 fp32 (16 KB)
 constexpr int kOffT = kOffW + kNB2 * kCH * 4;      // T: 32 x 32 fp64 (8 KB)
-constexpr int kOffRed = kOffT + kNB2 * kNB2 * 8;   // panel reductions: 8 warps x 32 x (s, c) floats
-constexpr int kOffOut = kOffRed + 8 * kNB2 * 2 * 4;  // panel broadcasts (512 bytes)
-constexpr int kMixSmem = kOffOut + 512;
+constexpr int kMixSmem = kOffT + kNB2 * kNB2 * 8;
 // the FP64 tree merge reuses the same buffer with the leaf kernel's plan
 constexpr int kMergeSmem = (int)kLeafSmemBytes;
 constexpr int kMixSmemTotal = kMixSmem > kMergeSmem ? kMixSmem : kMergeSmem;
@@ -80,30 +78,6 @@ __device__ __forceinline__ float vval_f(const float* Y, int64_t ldy, int64_t k, 
   if (i < d) return 0.f;
   if (i == d) return 1.f;
   return Y[i + d * ldy];
-}
-
-// Kahan-compensated FP32 accumulation, reduced in FP64
-struct KSum32 {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float x) {
-    const float y = x - c, t = s + y;
-    c = (t - s) - y;
-    s = t;
-  }
-  __device__ __forceinline__ double get() const { return (double)s - (double)c; }
-};
-
-// Compensated FP32 value s + c (TwoSum addition): the cross-thread sums of
-// the panel statistics stay at about double-float accuracy without FP64
-// arithmetic, which runs at a small fraction of the FP32 rate on this part.
-struct F2 {
-  float s, c;
-};
-__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
-  const float s = a.s + b.s;
-  const float bb = s - a.s;
-  const float e = (a.s - (s - bb)) + (b.s - bb);
-  return {s, e + a.c + b.c};
 }
 
 // ---------------------------------------------------------------------------
@@ -753,8 +727,6 @@ __global__ void __launch_bounds__(kMxThreads) leaf_qr_mixed_kernel(MixedArgs a) 
   const int64_t npan = (M + kNB2 - 1) / kNB2;
   float* Y = a.Yf + r0;
   double* sT = (double*)(msm + kOffT);
-  double* sred = (double*)(msm + kOffRed);
-  double* sout = (double*)(msm + kOffOut);
   if (a.xtype == PYLOM_F32)
     mixed_prologue<float>(a, Y, ldy, r0, h);
   else
