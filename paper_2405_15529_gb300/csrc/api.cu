@@ -5,6 +5,10 @@
 #include <cstring>
 #include <vector>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "kernels.h"
 
 using namespace pylom;
@@ -70,6 +74,20 @@ PhaseProfiler g_prof;
 bool aligned256(const void* p) { return ((uintptr_t)p & 255u) == 0; }
 
 }  // namespace
+
+cudaError_t pylom::ensure_dyn_smem(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& have = done[std::make_pair(dev, func)];
+  if (have >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) have = bytes;
+  return e;
+}
 
 void pylom::set_error_message(const char* fmt, ...) {
   va_list ap;

@@ -994,16 +994,10 @@ extern "C" pylom_status pylom_dmd(const void* X, int64_t N, int64_t M, int64_t l
   if (2 * hbytes <= kEigSmemCap) smem_mode = 2;
   else if (hbytes <= kEigSmemCap) smem_mode = 1;
   const size_t eig_smem = svbytes + (smem_mode == 2 ? 2 * hbytes : smem_mode == 1 ? hbytes : 0);
-  static bool attr = false;
-  cudaError_t e = cudaSuccess;
-  if (!attr) {
-    e = cudaFuncSetAttribute(dmd_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kEigSmemCap + sizeof(double) * 4096));
-    if (e != cudaSuccess) {
-      set_error_message("pylom_dmd: %s", cudaGetErrorString(e));
-      return PYLOM_ERR_CUDA;
-    }
-    attr = true;
+  cudaError_t e = ensure_dyn_smem((const void*)dmd_eig_kernel, kEigSmemCap + sizeof(double) * 4096);
+  if (e != cudaSuccess) {
+    set_error_message("pylom_dmd: %s", cudaGetErrorString(e));
+    return PYLOM_ERR_CUDA;
   }
   auto fail = [&](const char* what) {
     set_error_message("pylom_dmd: %s: %s", what, cudaGetErrorString(e));

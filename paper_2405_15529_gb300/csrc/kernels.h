@@ -103,6 +103,11 @@ cudaError_t launch_pod_backward(const TsqrState& fs, const double* UR, const dou
 // (FP32, ld N) on tcgen05, top M rows into the binary64 slots Z.
 cudaError_t launch_leaf_qt_mixed(const TsqrState& s, char* extra, float* C, int64_t r, double* Z, cudaStream_t st);
 
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device.  Function attributes belong to a device, so the setting
+// is remembered per (device, kernel); thread-safe.
+cudaError_t ensure_dyn_smem(const void* func, size_t bytes);
+
 // Records a message for pylom_last_error() on the calling host thread.
 void set_error_message(const char* fmt, ...);
 

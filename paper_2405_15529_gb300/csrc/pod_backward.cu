@@ -300,13 +300,7 @@ cudaError_t launch_pod_backward(const TsqrState& fs, const double* UR, const dou
   } else if (dU && r > 0) {
     bw_load_du_kernel<<<1024, 256, 0, st>>>(dU, lddu, w, physical, L.C, N, r);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    static bool attr = false;
-    if (!attr) {
-      e = cudaFuncSetAttribute(bw_leaf_qt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kLeafSmemBytes);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
+    if ((e = ensure_dyn_smem((const void*)bw_leaf_qt_kernel, kLeafSmemBytes)) != cudaSuccess) return e;
     bw_leaf_qt_kernel<<<(unsigned)P, kLeafThreads, kLeafSmemBytes, st>>>(fs, L.C, L.Z, r);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     for (int64_t step = 1; step < P; step <<= 1) {

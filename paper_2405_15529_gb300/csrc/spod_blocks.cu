@@ -328,13 +328,8 @@ extern "C" pylom_status pylom_spod_blocks(const void* D, int64_t N, int64_t T, i
     // tensor-core path
     spod_ftab_kernel<<<1, 256, 0, st>>>(Fhl, npwin, nblks);
     e = cudaGetLastError();
-    static bool tc_attr = false;
-    if (e == cudaSuccess && !tc_attr) {
-      e = cudaFuncSetAttribute(spod_dft_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFSmem);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(spod_dft_tc_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFSmem);
-      if (e == cudaSuccess) tc_attr = true;
-    }
+    if (e == cudaSuccess) e = ensure_dyn_smem((const void*)spod_dft_tc_kernel<float>, kFSmem);
+    if (e == cudaSuccess) e = ensure_dyn_smem((const void*)spod_dft_tc_kernel<double>, kFSmem);
     if (e == cudaSuccess) {
       const unsigned grid = (unsigned)((N + 127) / 128);
       if (dtype == PYLOM_F32)
@@ -349,12 +344,9 @@ extern "C" pylom_status pylom_spod_blocks(const void* D, int64_t N, int64_t T, i
     }
   } else if (e == cudaSuccess) {
     const size_t smem = sizeof(float) * ((size_t)npwin * kSpodThreads + 3 * (size_t)npwin);
-    static size_t smem_set = 0;
-    if (smem > 48 * 1024 && smem > smem_set) {
-      e = cudaFuncSetAttribute(spod_blocks_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(spod_blocks_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) smem_set = smem;
+    if (smem > 48 * 1024) {
+      e = ensure_dyn_smem((const void*)spod_blocks_kernel<float>, smem);
+      if (e == cudaSuccess) e = ensure_dyn_smem((const void*)spod_blocks_kernel<double>, smem);
     }
     if (e == cudaSuccess) {
       // scale: 1 / (mean(w) npwin sqrt(nBlks)); sum_j w_j = 0.54 npwin - 0.46 sum_j cos(2 pi j/(npwin-1))

@@ -322,12 +322,7 @@ cudaError_t launch_svd_fp64(const SvdState& s, const double* R, int64_t ldr, dou
                                   args, 0, st);
   if (e != cudaSuccess) return e;
   const size_t fsm = sizeof(double) * 2 * (size_t)s.M + sizeof(int) * (size_t)s.M;
-  static size_t fsm_set = 0;
-  if (fsm > 48 * 1024 && fsm > fsm_set) {
-    e = cudaFuncSetAttribute(svd_finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
-    if (e != cudaSuccess) return e;
-    fsm_set = fsm;
-  }
+  if (fsm > 48 * 1024 && (e = ensure_dyn_smem((const void*)svd_finalize_kernel, fsm)) != cudaSuccess) return e;
   svd_finalize_kernel<<<1, kFinThreads, fsm, st>>>(s, U, ldu, S, VT, ldvt, energy, r_max);
   return cudaGetLastError();
 }

@@ -200,12 +200,7 @@ cudaError_t launch_jacobi32_precondition(const SvdState& s, const double* R, int
   jacobi32_init_kernel<<<256, 256, 0, st>>>(s, R, ldr);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const size_t smem = sizeof(float) * ((size_t)2 * kJB * M + 4 * kJB * kJB);
-  static size_t smem_set = 0;
-  if (smem > smem_set) {
-    e = cudaFuncSetAttribute(jacobi32_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    smem_set = smem;
-  }
+  if ((e = ensure_dyn_smem((const void*)jacobi32_block_kernel, smem)) != cudaSuccess) return e;
   int dev = 0, sms = 0, per = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;

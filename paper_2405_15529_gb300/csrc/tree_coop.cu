@@ -90,18 +90,21 @@ __global__ void __launch_bounds__(kLeafThreads, 2) tree_coop_kernel(TsqrState s)
 
 cudaError_t launch_tree_coop(const TsqrState& s, cudaStream_t st) {
   if (s.P <= 1) return cudaSuccess;
-  static int grid = 0;
+  // co-resident grid, per device (occupancy after the shared-memory limit is raised)
+  static int grid_of[64] = {0};
   cudaError_t e;
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = ensure_dyn_smem((const void*)tree_coop_kernel, kLeafSmemBytes)) != cudaSuccess) return e;
+  int grid = (dev >= 0 && dev < 64) ? grid_of[dev] : 0;
   if (grid == 0) {
-    e = cudaFuncSetAttribute(tree_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeafSmemBytes);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    int sms = 0, per = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tree_coop_kernel, kLeafThreads, kLeafSmemBytes);
     if (e != cudaSuccess) return e;
     if (per < 1) return cudaErrorCooperativeLaunchTooLarge;
     grid = per * sms;
+    if (dev >= 0 && dev < 64) grid_of[dev] = grid;
   }
   TsqrState a = s;
   void* args[] = {&a};

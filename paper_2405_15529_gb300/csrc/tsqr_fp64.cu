@@ -344,16 +344,8 @@ void tsqr_state_carve(TsqrState& s, char* base, int64_t N, int64_t M, int64_t P,
 cudaError_t launch_tsqr_fp64(const TsqrState& s, const void* X, int64_t ldx, int xtype,
                              const double* w, int remove_mean, double* mean, cudaStream_t st) {
   cudaError_t e;
-  static bool attr_set = false;
-  if (!attr_set) {
-    e = cudaFuncSetAttribute(leaf_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kLeafSmemBytes);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(modes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kLeafSmemBytes);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  if ((e = ensure_dyn_smem((const void*)leaf_qr_kernel, kLeafSmemBytes)) != cudaSuccess) return e;
+  if ((e = ensure_dyn_smem((const void*)modes_kernel, kLeafSmemBytes)) != cudaSuccess) return e;
   LeafArgs a{s, X, ldx, xtype, w, remove_mean, mean};
   leaf_qr_kernel<<<(unsigned)s.Pl, kLeafThreads, kLeafSmemBytes, st>>>(a);
   e = cudaGetLastError();
@@ -402,13 +394,8 @@ cudaError_t launch_modes_fp64(const TsqrState& s, const double* Ur, int64_t ldur
 
 cudaError_t launch_leaf_modes_fp64(const TsqrState& s, int64_t r_fixed, const double* w, int physical, double* U,
                                    int64_t ldu, int64_t* r_out, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(modes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kLeafSmemBytes);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  const cudaError_t e = ensure_dyn_smem((const void*)modes_kernel, kLeafSmemBytes);
+  if (e != cudaSuccess) return e;
   modes_kernel<<<(unsigned)s.Pl, kLeafThreads, kLeafSmemBytes, st>>>(s, r_fixed, w, physical, U, ldu, r_out);
   return cudaGetLastError();
 }

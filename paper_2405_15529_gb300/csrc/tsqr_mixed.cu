@@ -886,15 +886,9 @@ size_t mixed_extra_bytes(int64_t N, int64_t M, int64_t P) {
 
 cudaError_t launch_tsqr_mixed(const TsqrState& s, char* extra, const void* X, int64_t ldx, int xtype,
                               const double* w, int remove_mean, double* mean, cudaStream_t st) {
-  static bool attr = false;
   cudaError_t e;
-  if (!attr) {
-    e = cudaFuncSetAttribute(leaf_qr_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMixSmemTotal);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(modes_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMixSmemTotal);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  if ((e = ensure_dyn_smem((const void*)leaf_qr_mixed_kernel, kMixSmemTotal)) != cudaSuccess) return e;
+  if ((e = ensure_dyn_smem((const void*)modes_mixed_kernel, kMixSmemTotal)) != cudaSuccess) return e;
   const int64_t npan = (s.M + kNB2 - 1) / kNB2;
   char* t2 = extra + align256(sizeof(float) * (size_t)s.N * s.M);
   char* pb = t2 + align256(sizeof(double) * (size_t)s.P * npan * kNB2 * kNB2);
@@ -918,14 +912,10 @@ cudaError_t launch_modes_mixed(const TsqrState& s, char* extra, const double* Ur
 }
 
 cudaError_t launch_leaf_qt_mixed(const TsqrState& s, char* extra, float* C, int64_t r, double* Z, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(leaf_qt_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kMixSmemTotal);
+  {
+    cudaError_t e = ensure_dyn_smem((const void*)leaf_qt_mixed_kernel, kMixSmemTotal);
+    if (e == cudaSuccess) e = ensure_dyn_smem((const void*)modes_mixed_kernel, kMixSmemTotal);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(modes_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMixSmemTotal);
-    if (e != cudaSuccess) return e;
-    attr = true;
   }
   const float* Yf = (const float*)extra;
   const double* T2 = (const double*)(extra + align256(sizeof(float) * (size_t)s.N * s.M));
