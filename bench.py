@@ -809,6 +809,36 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+def run_case(name: str) -> int:
+    """Fixed workloads for kernel captures (no JSON line):
+    spod16        the batched-SVD section on the first 16 SPOD bins, one replay;
+    mixed1808     two mixed-precision POD calls on the 2,000,000 x 1808 wave field
+                  (64 waves, power-law amplitudes, noise 1e-4, mean removed, 99 %, r <= 128),
+                  phases printed;
+    mixedwave512  two mixed-precision POD calls on a 1,048,576 x 512 wave field (same recipe)."""
+    import torch
+    import paper_2405_15529_gb300 as pg
+    import synth
+    dev = torch.device("cuda", 0)
+    if name == "spod16":
+        out = bench_spod(argparse.Namespace(spod_bins=16, spod_steps=1, tune=False, warmup=1), dev)
+        print("ms", round(out["ms_per_step"], 1), out["status"])
+        return 0
+    N, M = {"mixed1808": (2_000_000, 1808), "mixedwave512": (1 << 20, 512)}[name]
+    XT = synth.waves_torch(N, M, 64, "powerlaw", 1e-4, 5, dev, dtype=torch.float32, row_chunk=1 << 18)
+    X = XT.t()
+    res = pg.pod(X, remove_mean=True, energy=0.99, r_max=128, prec=pg.PREC_MIXED_3XTF32)
+    torch.cuda.synchronize()
+    pg.profile_begin(1)
+    res = pg.pod(X, remove_mean=True, energy=0.99, r_max=128, prec=pg.PREC_MIXED_3XTF32, check=False)
+    torch.cuda.synchronize()
+    ph, n = pg.profile_end()
+    st, r, sw = pg.workspace_status(res.workspace)
+    print(json.dumps({k: round(v / max(n, 1), 2) for k, v in ph.items()} | {"r": r, "sweeps": sw, "status": st,
+                                                                           "N": N, "M": M}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -836,11 +866,15 @@ def main():
     ap.add_argument("--spod-steps", type=int, default=3)
     ap.add_argument("--spod-bins", type=int, default=256)
     ap.add_argument("--tune", action="store_true", help="autotune SPOD leaf heights (cached)")
+    ap.add_argument("--case", choices=["spod16", "mixed1808", "mixedwave512"], default=None,
+                    help="run one fixed workload for a kernel capture instead of the benchmark")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)
     local_rank = _env_int("LOCAL_RANK", 0)
+    if args.case:
+        return run_case(args.case)
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if world > 1:
