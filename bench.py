@@ -94,6 +94,33 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+_PROBE = None
+
+
+def probe_peak(kind: str) -> float:
+    """Measured TFLOP/s of this GPU from the benchmark's own probes
+    (bench_probe.cu): 'mma' binary64 mma.sync.m8n8k4, 'fma' binary64 FMA,
+    'ffma' binary32 FMA."""
+    import ctypes
+    import torch
+    global _PROBE
+    if _PROBE is None:
+        from paper_2405_15529_gb300 import _build
+        lib = ctypes.CDLL(_build.build_probe())
+        lib.bench_probe_scratch_bytes.restype = ctypes.c_size_t
+        lib.bench_probe_peak.restype = ctypes.c_int
+        lib.bench_probe_peak.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.c_void_p]
+        _PROBE = lib
+    scratch = torch.empty(_PROBE.bench_probe_scratch_bytes(), dtype=torch.uint8, device="cuda")
+    out = ctypes.c_double(0.0)
+    rc = _PROBE.bench_probe_peak({"mma": 0, "fma": 1, "ffma": 2}[kind], ctypes.c_void_p(scratch.data_ptr()),
+                                 ctypes.byref(out), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != 0:
+        raise RuntimeError(f"bench_probe_peak({kind}) failed with code {rc}")
+    return float(out.value)
+
+
 def rank_max(value: float, device=None) -> float:
     """Max of a per-rank time over the job's ranks (the slowest rank sets the
     step time); the value itself on a single process."""
@@ -111,20 +138,110 @@ def job_gbs(bytes_per_rank: float, ms: float, world: int) -> float:
     return world * bytes_per_rank / (ms * 1e-3) / 1e9
 
 
-def cpu_baseline(n_rows: int, M: int, seed_shift: int = 0):
-    """The FP64 oracle, as it stands, on a row sample of the workload.
+def cpu_baseline(n_rows: int, M: int, seed_shift: int = 0, X=None, w=None):
+    """The FP64 oracle, as it stands, on the workload: on the given host
+    matrix X (N x M, with weights w) when passed -- the full workload -- else
+    on a freshly generated row sample of it.
     Returns (GB/s of X, seconds, threads, sample description)."""
     import numpy as np
     import oracle
     import synth
-    X, w, s = synth.known_spectrum(n_rows, M, weights=True, seeds=(2 + seed_shift, 3, 4))
+    if X is None:
+        X, w, s = synth.known_spectrum(n_rows, M, weights=True, seeds=(2 + seed_shift, 3, 4))
+        what = f"a {n_rows} x {M} row sample of the workload (same spectrum, weights, energy {ENERGY})"
+    else:
+        n_rows = X.shape[0]
+        what = f"the full {n_rows} x {M} workload (the same X and weights the GPU step reads, energy {ENERGY})"
     t0 = time.perf_counter()
     res = oracle.pod(X, w=w, remove_mean=False, energy=ENERGY)
     dt = time.perf_counter() - t0
     gbs = n_rows * M * 8 / dt / 1e9
-    desc = (f"oracle.pod on a {n_rows} x {M} row sample of the workload (same spectrum, weights, "
-            f"energy {ENERGY}; r={res['r']}), one run")
+    desc = f"oracle.pod on {what}; r={res['r']}; one run"
     return gbs, dt, oracle.num_threads(), desc
+
+
+def fp64_matmul_tflops(dev, n=4096, reps=3):
+    """TFLOP/s of the library's binary64 product (pylom_matmul, the FP64
+    tensor pipe) on an n x n x n problem whose flops are known (2 n^3): a
+    cross-check of the probe's FP64 peak by a kernel doing real work."""
+    import torch
+    import paper_2405_15529_gb300 as pg
+    g = torch.Generator(device=dev).manual_seed(9)
+    A = torch.randn((n, n), dtype=torch.float64, device=dev, generator=g)
+    B = torch.randn((n, n), dtype=torch.float64, device=dev, generator=g)
+    pg.matmul(A, B)
+    torch.cuda.synchronize()
+    best = 0.0
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        C = pg.matmul(A, B)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 2.0 * n ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    del A, B, C
+    torch.cuda.empty_cache()
+    return best
+
+
+def h2d_sweep(Xh, dev, sizes_mb=(64, 512, 2048), chunk_mb=256):
+    """Host-to-device copy rate from the page-locked buffer Xh at several
+    sizes, as one copy and as a train of chunk_mb copies on a side stream
+    (diagnostics of the end-to-end upload; not part of any timed step)."""
+    import torch
+    flat = Xh.view(-1).view(torch.uint8)
+    total = flat.numel()
+    dst = torch.empty(total, dtype=torch.uint8, device=dev)
+    out = {}
+    side = torch.cuda.Stream(device=dev)
+
+    def rate(nbytes, chunked):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(side):
+            ev0.record(side)
+            if chunked:
+                step = chunk_mb << 20
+                for o in range(0, nbytes, step):
+                    e = min(nbytes, o + step)
+                    dst[o:e].copy_(flat[o:e], non_blocking=True)
+            else:
+                dst[:nbytes].copy_(flat[:nbytes], non_blocking=True)
+            ev1.record(side)
+        ev1.synchronize()
+        return nbytes / (ev0.elapsed_time(ev1) * 1e-3) / 1e9
+
+    for mb in list(sizes_mb) + [total >> 20]:
+        nb = min(total, mb << 20)
+        rate(nb, False)                     # warm
+        out[f"{nb >> 20}MB_one_copy_gbs"] = rate(nb, False)
+        out[f"{nb >> 20}MB_{chunk_mb}MB_chunks_gbs"] = rate(nb, True)
+    del dst
+    torch.cuda.empty_cache()
+    return out
+
+
+def gpu_numa_info(local_rank):
+    """Where the GPU and this process sit (sysfs), recorded beside the
+    end-to-end number."""
+    info = {}
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(local_rank)
+        bus = f"{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        info["pci"] = bus
+        for key in ("numa_node", "local_cpulist"):
+            try:
+                with open(f"/sys/bus/pci/devices/{bus}/{key}") as f:
+                    info[key] = f.read().strip()
+            except OSError:
+                pass
+    except Exception as exc:  # noqa: BLE001 - diagnostics only
+        info["error"] = str(exc)[:200]
+    try:
+        info["process_cpus"] = len(os.sched_getaffinity(0))
+    except OSError:
+        pass
+    return info
 
 
 def bench_adjoint(args, dev):
@@ -433,6 +550,29 @@ def bench_streamed(args, dev):
 C3_N, C3_M, C3_RMAX = 10_000_000, 1808, 128
 
 
+def c3_cpu_baseline(N, M, rmax, rows=(8192, 16384)):
+    """The FP64 oracle on row samples of the 1808-column wave field, as it
+    stands: the POD of each sample is timed whole, its time fitted as
+    a + b * rows (the QR and modes grow with the rows, the Jacobi SVD of the
+    1808 x 1808 R does not) and extrapolated to N rows.  Minutes of CPU."""
+    import oracle
+    import synth
+    ts = []
+    for n in rows:
+        X = synth.waves(n, M, n_waves=64, amp="powerlaw", noise=1e-4, seed=5)
+        t0 = time.perf_counter()
+        oracle.pod(X, remove_mean=True, energy=ENERGY, r_max=rmax)
+        ts.append(time.perf_counter() - t0)
+    b = (ts[1] - ts[0]) / (rows[1] - rows[0])
+    a = ts[0] - b * rows[0]
+    t_full = a + b * N
+    return {"value": N * M * 4 / t_full / 1e9, "unit": "GB/s of X (float32)", "cores": oracle.num_threads(),
+            "kind": "oracle", "extrapolated": True, "seconds_full_size": t_full,
+            "sample": f"oracle.pod on {rows[0]} and {rows[1]} x {M} samples of the wave field "
+                      f"({ts[0]:.1f} s, {ts[1]:.1f} s), fitted as a + b*rows and extrapolated linearly in "
+                      f"rows to {N}"}
+
+
 def bench_waves_1808(args, dev):
     """The 10,000,000 x 1808 float32 wake-like field (64 traveling waves,
     power-law amplitudes, noise 1e-4; 72.3 GB) through the mixed path, timed,
@@ -513,9 +653,31 @@ def bench_waves_1808(args, dev):
     tf32_3x = peaks.get("bf16_tflops", 1900.0) * 0.5 / 3.0     # nominal tf32/bf16 = 1/2; three MMAs per product
     t_roof = max(bytes_x / (hbm * 1e9), 2.0 * N * M * M / (tf32_3x * 1e12))
     leaf_ms = mix["phases_ms"]["leaf_qr_tree"]
+    # dominant kernel of the mixed step: the leaves (FP32 panels + 3xTF32
+    # trailing updates, 2NM^2 - (2/3)PM^3 flops as three TF32 products) and
+    # the binary64 tree that follows them in the same phase
+    P = pg.leaf_count(N, M, 0)
+    P = min(P, 152) if P > 152 else P
+    leaf_flops = 2.0 * N * M * M - (2.0 / 3.0) * P * M ** 3
+    tree_flops = (P - 1) * (2.0 / 3.0) * M ** 3
+    fp64_peak = probe_peak("mma")
+    t_kernel_roof = leaf_flops / (tf32_3x * 1e12) + tree_flops / (fp64_peak * 1e12)
+    roofline = {"bound": "tensor", "achieved": leaf_flops / (leaf_ms * 1e-3) / 1e12, "peak": tf32_3x,
+                "unit": "TFLOP/s", "frac": t_kernel_roof / (leaf_ms * 1e-3), "traffic": None,
+                "kernel": "leaf_qr_mixed_kernel + tree_coop_kernel (phase leaf_qr_tree)",
+                "peak_source": "3xTF32 = measured bf16 burst x nominal tf32/bf16 (1/2) / 3; the tree's "
+                               "binary64 flops at the measured FP64 mma probe rate",
+                "algorithmic_flops_per_launch": {"leaf_3xtf32": leaf_flops, "tree_fp64": tree_flops},
+                "frac_formula": "(leaf_flops/tf32_3x_peak + tree_flops/fp64_peak) / phase time",
+                "ms_per_launch": leaf_ms, "leaves": P}
+    cpu = {"skipped": "the oracle's unblocked QR and cyclic Jacobi at 1808 columns take minutes even on a "
+                      "row sample; run bench.py --c3-cpu for the extrapolated figure"}
+    if args.c3_cpu:
+        cpu = c3_cpu_baseline(N, M, rmax)
     return {"workload": f"waves64_powerlaw_{N}x{M}_f32_mean_removed_energy0.99_rmax{rmax}",
             "status": [mix["status"], f64["status"]], "r": [mix["r"], f64["r"]],
-            "ms_per_step": mix["ms"], "steps": args.c3_steps, "warmup": 1,
+            "ms_per_step": mix["ms"], "steps": args.c3_steps, "warmup": 1, "roofline": roofline,
+            "cpu_baseline": cpu,
             "value": bytes_x / (mix["ms"] * 1e-3) / 1e9, "unit": "GB/s of X (float32)",
             "phases_ms_per_step": mix["phases_ms"], "jacobi_sweeps": mix["sweeps"],
             "fp64_path_ms_same_x": f64["ms"], "fp64_path_phases_ms": f64["phases_ms"],
@@ -547,7 +709,9 @@ def bench_spod(args, dev):
          for f, (n, nb) in enumerate(zip(Ns, Nbs))]
     torch.cuda.synchronize()
     prec = pg.PREC_MIXED_3XTF32
+    t_tune = time.perf_counter()
     leaf_rows = tune.leaf_rows_for(Ns, Nbs, prec, tune=args.tune)
+    t_tune = time.perf_counter() - t_tune
     b = pg.BatchedSVD(Q, kmodes=8, prec=prec, leaf_rows=leaf_rows)
     b.capture()
     b.replay()
@@ -563,7 +727,7 @@ def bench_spod(args, dev):
     in_bytes = float(sum(int(n) * int(nb) * 8 for n, nb in zip(Ns, Nbs)))
     out_bytes = float(sum(int(n) * min(8, int(nb)) * 8 for n, nb in zip(Ns, Nbs)))
     flops = float(sum(8.0 * int(n) * int(nb) ** 2 for n, nb in zip(Ns, Nbs)))
-    peak_ffma = pg.probe_fp64_peak("ffma")
+    peak_ffma = probe_peak("ffma")
     # oracle check on the two smallest bins (complex128 oracle on the same complex64 data)
     small = np.argsort(Ns * Nbs ** 2)[:2]
     errs = []
@@ -581,7 +745,8 @@ def bench_spod(args, dev):
                         "peak_source": "measured live: FP32 FMA throughput probe",
                         "hbm_gbs_of_algorithmic_bytes": (in_bytes + out_bytes) / (ms * 1e-3) / 1e9},
            "sigma_err_vs_oracle_smallest_bins": errs,
-           "leaf_rows_tuned": bool(args.tune)}
+           "leaf_rows_tuned": bool(args.tune), "tune_seconds_untimed": t_tune,
+           "leaf_rows_histogram": {str(h): leaf_rows.count(h) for h in sorted(set(leaf_rows))}}
     del Q, b
     torch.cuda.empty_cache()
     return out
@@ -651,8 +816,9 @@ def run_ours(args, rank, world, local_rank):
     sig_err = float(np.max(np.abs(S_np - s)) / s[0])
 
     # FP64 roofline denominators, measured on this GPU
-    peak_mma = pg.probe_fp64_peak("mma")
-    peak_fma = pg.probe_fp64_peak("fma")
+    peak_mma = probe_peak("mma")
+    peak_fma = probe_peak("fma")
+    mm_tflops = fp64_matmul_tflops(dev)
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local_rank)
@@ -712,7 +878,7 @@ def run_ours(args, rank, world, local_rank):
             nonlocal d2h
             if record:
                 ev[0].record()
-            Xd.copy_(Xh, non_blocking=True)
+            pg.upload(Xd, Xh)                 # 256 MB pieces (one multi-GB copy runs at a fraction of the link)
             wd.copy_(wh, non_blocking=True)
             if record:
                 ev[1].record()
@@ -752,11 +918,19 @@ def run_ours(args, rank, world, local_rank):
                "h2d_bytes_per_step": N * M * 8 + N * 8, "d2h_bytes_per_step": d2h,
                "split_ms_one_step": split, "host_buffers_pinned": bool(Xh.is_pinned() and Uh.is_pinned()),
                "h2d_gbs_one_step": (N * M * 8 + N * 8) / (split["h2d"] * 1e-3) / 1e9 if split["h2d"] > 0 else None}
+        if not args.no_h2d_sweep:
+            e2e["h2d_sweep_outside_timed_region"] = h2d_sweep(Xh, dev)
+        e2e["placement"] = gpu_numa_info(local_rank)
         del Xh, Uh, host
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        gbs, dt, thr, desc = cpu_baseline(args.cpu_rows, M)
+        if args.cpu_rows >= N:
+            Xc = XT.cpu().numpy().T          # the same X (column-major N x M) on the host
+            gbs, dt, thr, desc = cpu_baseline(N, M, X=Xc, w=w.cpu().numpy())
+            del Xc
+        else:
+            gbs, dt, thr, desc = cpu_baseline(args.cpu_rows, M)
         cpu = {"value": gbs, "unit": "GB/s", "cores": thr, "kind": "oracle", "sample": desc,
                "seconds": dt}
 
@@ -792,13 +966,15 @@ def run_ours(args, rank, world, local_rank):
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_mma, "unit": "TFLOP/s",
                          "frac": achieved / peak_mma, "traffic": None,
                          "kernel": "leaf_qr_kernel (leaf Householder QR + tree merges)",
-                         "peak_source": "measured live: FP64 mma.sync.m8n8k4 throughput probe "
-                                        "(MEASURED_PEAKS.json has no FP64 figure)",
+                         "peak_source": "measured live: FP64 mma.sync.m8n8k4 throughput probe with "
+                                        "independent chains (bench_probe.cu; MEASURED_PEAKS.json has no "
+                                        "FP64 figure); cross-checked by the FP64 4096^3 product",
                          "algorithmic_flops_per_launch": flops_leaf, "ms_per_launch": leaf_ms},
             "pct_roofline_pod": {"value": pct_roof,
                                  "formula": "max(bytes_X/HBM_peak, 2NM^2/FP64_mma_peak) / step time",
                                  "hbm_peak_gbs": hbm_peak, "fp64_mma_tflops": peak_mma,
-                                 "fp64_fma_tflops": peak_fma},
+                                 "fp64_fma_tflops": peak_fma,
+                                 "fp64_matmul_4096cubed_tflops": mm_tflops},
             "phases_ms_per_step": {k: v / max(ncalls, 1) for k, v in phases.items()},
             "accuracy": {"sigma_max_abs_err_over_smax_vs_closed_form": sig_err, "r": r,
                          "jacobi_sweeps": sweeps},
@@ -847,10 +1023,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--rows", type=int, default=N_FULL)
     ap.add_argument("--leaf-rows", type=int, default=0)
-    ap.add_argument("--cpu-rows", type=int, default=1 << 17)
+    ap.add_argument("--cpu-rows", type=int, default=N_FULL,
+                    help="rows of the oracle's CPU baseline (>= --rows: the full workload)")
     ap.add_argument("--ref-rows", type=int, default=1 << 16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-h2d-sweep", action="store_true", help="skip the upload-rate diagnostics")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-spod", action="store_true")
@@ -861,11 +1039,14 @@ def main():
     ap.add_argument("--stream-chunk", type=int, default=1 << 20)
     ap.add_argument("--stream-steps", type=int, default=2)
     ap.add_argument("--c3-rows", type=int, default=C3_N)
-    ap.add_argument("--c3-steps", type=int, default=1)
+    ap.add_argument("--c3-steps", type=int, default=3)
+    ap.add_argument("--c3-cpu", action="store_true",
+                    help="time the oracle on row samples of the 10,000,000 x 1808 workload (minutes)")
     ap.add_argument("--adj-steps", type=int, default=3)
     ap.add_argument("--spod-steps", type=int, default=3)
     ap.add_argument("--spod-bins", type=int, default=256)
-    ap.add_argument("--tune", action="store_true", help="autotune SPOD leaf heights (cached)")
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="run the SPOD bins with the built-in leaf heights instead of the autotuned ones")
     ap.add_argument("--case", choices=["spod16", "mixed1808", "mixedwave512"], default=None,
                     help="run one fixed workload for a kernel capture instead of the benchmark")
     args = ap.parse_args()

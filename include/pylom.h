@@ -219,6 +219,52 @@ pylom_status pylom_pod_streamed(const void* X, int64_t N, int64_t M, int64_t ldx
                                 void* stream);
 
 /* ------------------------------------------------------------------------
+ * Row-sharded POD -- the paper's parallel form (Sec. 3.1, Alg. 1: every
+ * process owns a block of rows, a binary tree reduces their R factors, the
+ * result is broadcast back down the tree), with the row blocks as shards
+ * that may live on different devices.  The only data exchanged between
+ * shards is the G factors R_g (G * M * M doubles), which the caller
+ * gathers (an all-gather across devices; Alg. 4's all_reduce is the same
+ * collective pattern).  Per shard g holding rows X_g (N_g x M), in order:
+ *   pylom_pod_shard_factor  a1-a3 on X_g: mean removal and sqrt(w) weights
+ *       (the mean is per row, so local), leaf QR and the tree of the shard's
+ *       own leaves; writes R_g (M x M upper triangular, zeros below, ldr >=
+ *       M).  The reflectors stay in the shard's workspace ws, which must be
+ *       kept unchanged until pylom_pod_shard_modes.
+ *   (caller) gather R_0 .. R_{G-1} into one stack, shard g at Rstack +
+ *       g M M (each M x M, ld M), on every shard.
+ *   pylom_pod_rstack  replicated on every shard: the top of the tree over
+ *       the G stacked factors with Alg. 1's XOR pairing (shard ids in place
+ *       of process ids; an unpaired shard passes its R up), the SVD of the
+ *       root R (Eq. svdqr2), the truncation (energy, r_max as in
+ *       pylom_pod), and the top-down pass: B receives G blocks of
+ *       M x r_max (ld M), block g at B + g M r_max, the rows of
+ *       Q_top [U_r; 0] that belong to shard g.  S (M), VT (M x M, ldvt >= M)
+ *       as pylom_pod.  r_out: device int64, the rank r.
+ *   pylom_pod_shard_modes  a6-a7 on the shard: the top-down pass through
+ *       its own tree from B_g (block g of B) and U_g = Q_g [B_g; 0] for the
+ *       shard's rows; r is the device int64 from pylom_pod_rstack.  U: N_g x
+ *       r_max (ldu >= N_g), binary64 for PYLOM_PREC_FP64, binary32 for
+ *       PYLOM_PREC_MIXED_3XTF32; mode_kind and w as pylom_pod.
+ * N_g, M, leaf_rows, r_max, xtype and prec must be the same in a shard's
+ * factor and modes calls.  Each shard's rows must satisfy N_g >= M.  The
+ * stacked result equals pylom_pod of the stacked X up to rounding (the tree
+ * pairs differ).  Device statuses go to the respective workspaces
+ * (pylom_workspace_status).  Asynchronous on `stream`.
+ * ------------------------------------------------------------------------ */
+size_t pylom_pod_shard_workspace_size(int64_t N, int64_t M, int64_t leaf_rows, int64_t r_max, int xtype, int prec);
+pylom_status pylom_pod_shard_factor(const void* X, int64_t N, int64_t M, int64_t ldx, int xtype, const double* w,
+                                    int remove_mean, int64_t leaf_rows, int64_t r_max, double* mean, double* R,
+                                    int64_t ldr, int prec, void* ws, size_t ws_bytes, void* stream);
+size_t pylom_pod_rstack_workspace_size(int64_t G, int64_t M, int64_t r_max);
+pylom_status pylom_pod_rstack(const double* Rstack, int64_t G, int64_t M, double energy, int64_t r_max, double* S,
+                              double* VT, int64_t ldvt, double* B, int64_t* r_out, void* ws, size_t ws_bytes,
+                              void* stream);
+pylom_status pylom_pod_shard_modes(const double* Bg, const int64_t* r, int64_t N, int64_t M, int64_t leaf_rows,
+                                   int64_t r_max, const double* w, int mode_kind, void* U, int64_t ldu, int prec,
+                                   void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
  * pylom_pod_backward -- hand-written adjoint of pylom_pod (no counterpart in
  * the paper; it differentiates the composition of Alg. 2, Alg. 1 and Eqs.
  * svdqr1-svdqr3).  Given cotangents dU (of the r returned modes), dS and
@@ -359,6 +405,10 @@ pylom_status pylom_svd_batched_run(const pylom_batched_plan* plan, void* ws, dou
  * 4 number of leaf items; -1 on a bad argument. */
 int64_t pylom_svd_batched_plan_info(const pylom_batched_plan* plan, int bin, int what);
 void pylom_svd_batched_plan_destroy(pylom_batched_plan* plan);
+/* Longest leaf a bin gets at precision prec (1024 rows for complex64
+ * leaves, 512 for complex128): a leaf height hint above it is split into
+ * more leaves.  -1 for a bad prec.  Host only. */
+int64_t pylom_svd_batched_max_leaf_rows(int prec);
 
 /* ------------------------------------------------------------------------
  * pylom_matmul -- local product of Alg. 4 (matmul_paral) on one device:
@@ -385,12 +435,40 @@ pylom_status pylom_matmul(int transA, const double* A, const double* B, double* 
  *  info   device int[2] or NULL: receives the device status (pylom_status)
  *         and the Jacobi sweeps used, stream-ordered after the SVD.
  * The first call on a device looks up the array's device address (once per
- * device); make it before any stream capture.  All calls share the array:
- * calls that may overlap on the GPU race and must be ordered on one stream.
+ * device); make it before any stream capture.  The address is kept for the
+ * life of the process, so after cudaDeviceReset on a device this entry point
+ * must not be called there again without reloading the library.  Devices
+ * with an index of 64 or more return PYLOM_ERR_UNSUPPORTED.  All calls share
+ * the array: calls that may overlap on the GPU race and must be ordered on
+ * one stream.
  * ------------------------------------------------------------------------ */
 pylom_status pylom_svd_small_noalloc(const double* R, int64_t M, int64_t ldr, double* U,
                                      int64_t ldu, double* S, double* VT, int64_t ldvt,
                                      int max_sweeps, int* info, void* stream);
+
+/* ------------------------------------------------------------------------
+ * pylom_wait_selftest -- runs one of the library's bounded device waits into
+ * its time limit on purpose (failure detection; no counterpart in the
+ * paper), so that the time-out path can be tested without hanging the GPU.
+ * Every cooperative kernel of the library waits on other thread blocks only
+ * through these two forms, each polling the GPU's global timer:
+ *   kind 0  the grid barrier: `blocks` thread blocks (1..1024) arrive at a
+ *           barrier that expects blocks + 1 arrivals, so nothing releases it;
+ *           each block then enters a second barrier, which must return at
+ *           once because the first one timed out;
+ *   kind 1  the mbarrier wait of the tcgen05 commits: one block waits on an
+ *           mbarrier that nothing arrives on (`blocks` is ignored).
+ * Each wait gives up after limit_ms milliseconds (0 < limit_ms <= 2000; the
+ * library's own kernels use 2000), records PYLOM_ERR_TIMEOUT in the
+ * workspace header and returns, so the kernel ends and the context stays
+ * usable.  gave_up: device unsigned or NULL, receives the number of blocks
+ * whose waits gave up.  ws: >= pylom_wait_selftest_workspace_size() bytes,
+ * 256-byte aligned; read the outcome with pylom_workspace_status
+ * (PYLOM_ERR_TIMEOUT).  Asynchronous on `stream`.
+ * ------------------------------------------------------------------------ */
+size_t pylom_wait_selftest_workspace_size(void);
+pylom_status pylom_wait_selftest(int kind, int blocks, double limit_ms, unsigned* gave_up, void* ws,
+                                 size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------
  * Phase profiler (measurement support; no counterpart in the paper).

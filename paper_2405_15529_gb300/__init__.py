@@ -36,13 +36,16 @@ EXPORTS = (
     "pylom_pod_workspace_size", "pylom_pod", "pylom_tsqr_workspace_size", "pylom_tsqr",
     "pylom_svd_small_workspace_size", "pylom_svd_small", "pylom_matmul_workspace_size",
     "pylom_matmul", "pylom_profile_begin", "pylom_profile_end",
-    "pylom_probe_scratch_bytes", "pylom_probe_fp64_peak", "pylom_svd_small_noalloc",
+    "pylom_svd_small_noalloc",
     "pylom_pod_backward_workspace_size", "pylom_pod_backward",
     "pylom_svd_batched_plan", "pylom_svd_batched_bind", "pylom_svd_batched_run",
-    "pylom_svd_batched_plan_info", "pylom_svd_batched_plan_destroy",
+    "pylom_svd_batched_plan_info", "pylom_svd_batched_plan_destroy", "pylom_svd_batched_max_leaf_rows",
     "pylom_spod_shape", "pylom_spod_blocks_workspace_size", "pylom_spod_blocks", "pylom_spod_order",
     "pylom_pod_streamed_workspace_size", "pylom_pod_streamed", "pylom_pod_streamed_leaf_rows",
     "pylom_dmd_workspace_size", "pylom_dmd",
+    "pylom_wait_selftest_workspace_size", "pylom_wait_selftest",
+    "pylom_pod_shard_workspace_size", "pylom_pod_shard_factor", "pylom_pod_rstack_workspace_size",
+    "pylom_pod_rstack", "pylom_pod_shard_modes",
 )
 PROFILE_PHASES = ("leaf_qr_tree", "svd_small", "down_pass", "modes")
 
@@ -136,9 +139,24 @@ def load_library(path: str = LIB_PATH):
     lib.pylom_svd_batched_plan_destroy.argtypes = [_vp]
     lib.pylom_svd_small_noalloc.restype = _int
     lib.pylom_svd_small_noalloc.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _int, _vp, _vp]
-    lib.pylom_probe_scratch_bytes.restype = _sz
-    lib.pylom_probe_fp64_peak.restype = _int
-    lib.pylom_probe_fp64_peak.argtypes = [_int, _vp, ctypes.POINTER(ctypes.c_double), _vp]
+    lib.pylom_svd_batched_max_leaf_rows.restype = _i64
+    lib.pylom_svd_batched_max_leaf_rows.argtypes = [_int]
+    lib.pylom_pod_shard_workspace_size.restype = _sz
+    lib.pylom_pod_shard_workspace_size.argtypes = [_i64, _i64, _i64, _i64, _int, _int]
+    lib.pylom_pod_shard_factor.restype = _int
+    lib.pylom_pod_shard_factor.argtypes = [_vp, _i64, _i64, _i64, _int, _vp, _int, _i64, _i64, _vp, _vp, _i64,
+                                           _int, _vp, _sz, _vp]
+    lib.pylom_pod_rstack_workspace_size.restype = _sz
+    lib.pylom_pod_rstack_workspace_size.argtypes = [_i64, _i64, _i64]
+    lib.pylom_pod_rstack.restype = _int
+    lib.pylom_pod_rstack.argtypes = [_vp, _i64, _i64, _dbl, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _sz, _vp]
+    lib.pylom_pod_shard_modes.restype = _int
+    lib.pylom_pod_shard_modes.argtypes = [_vp, _vp, _i64, _i64, _i64, _i64, _vp, _int, _vp, _i64, _int, _vp, _sz,
+                                          _vp]
+    lib.pylom_wait_selftest_workspace_size.restype = _sz
+    lib.pylom_wait_selftest_workspace_size.argtypes = []
+    lib.pylom_wait_selftest.restype = _int
+    lib.pylom_wait_selftest.argtypes = [_int, _int, _dbl, _vp, _vp, _sz, _vp]
     _lib = lib
     return lib
 
@@ -200,17 +218,43 @@ def profile_end():
     return dict(zip(PROFILE_PHASES, list(arr))), int(n.value)
 
 
-def probe_fp64_peak(kind: str = "mma") -> float:
-    """Measured TFLOP/s of this GPU: kind 'mma' (FP64 tensor pipe,
-    mma.sync.m8n8k4.f64), 'fma' (scalar FP64 FMA) or 'ffma' (FP32 FMA)."""
+def wait_selftest(kind: str = "grid", blocks: int = 16, limit_ms: float = 2.0, stream=None):
+    """Run one bounded device wait into its limit (pylom_wait_selftest):
+    kind 'grid' (the grid barrier) or 'mbarrier' (the tcgen05 commit wait).
+    Returns (device status, number of blocks whose waits gave up)."""
     torch = _torch()
     lib = load_library()
-    scratch = torch.empty(lib.pylom_probe_scratch_bytes(), dtype=torch.uint8, device="cuda")
-    out = ctypes.c_double(0.0)
-    st = lib.pylom_probe_fp64_peak({"mma": 0, "fma": 1, "ffma": 2}[kind], _dptr(scratch), ctypes.byref(out),
-                                   _stream(None))
-    _raise(st, "pylom_probe_fp64_peak")
-    return float(out.value)
+    ws = torch.zeros(lib.pylom_wait_selftest_workspace_size(), dtype=torch.uint8, device="cuda")
+    gave = torch.zeros(1, dtype=torch.int32, device="cuda")
+    _raise(lib.pylom_wait_selftest({"grid": 0, "mbarrier": 1}[kind], int(blocks), float(limit_ms), _dptr(gave),
+                                   _dptr(ws), ws.numel(), _stream(stream)), "pylom_wait_selftest")
+    st = lib.pylom_workspace_status(_dptr(ws), _stream(stream), None, None)
+    return int(st), int(gave.item())
+
+
+def upload(dst, src, chunk_bytes: int = 256 << 20, stream=None):
+    """Host-to-device copy of a page-locked host tensor into a device tensor
+    of the same size, issued as one cudaMemcpyAsync per chunk_bytes slice.
+    On GB300 one copy of several GB from page-locked memory ran at 20-55
+    GB/s while 256 MB pieces ran at 211 GB/s (measured inside the
+    benchmark), so large inputs are moved in pieces."""
+    torch = _torch()
+    if not (dst.is_contiguous() and src.is_contiguous()) or dst.numel() * dst.element_size() != \
+            src.numel() * src.element_size():
+        raise ValueError("upload needs contiguous tensors of the same size in bytes")
+    d = dst.view(-1).view(torch.uint8)
+    s = src.view(-1).view(torch.uint8)
+    ctx = torch.cuda.stream(stream) if stream is not None else None
+    if ctx:
+        ctx.__enter__()
+    try:
+        for o in range(0, d.numel(), chunk_bytes):
+            e = min(d.numel(), o + chunk_bytes)
+            d[o:e].copy_(s[o:e], non_blocking=True)
+    finally:
+        if ctx:
+            ctx.__exit__(None, None, None)
+    return dst
 
 
 def leaf_count(N: int, M: int, leaf_rows: int = 0) -> int:
@@ -616,6 +660,11 @@ def pod_autograd(X, r, w=None, remove_mean=False, mode_kind=MODES_ORTHONORMAL, l
     if _PodFn is None:
         _PodFn = _make_pod_function()
     return _PodFn.apply(X, w, int(r), bool(remove_mean), int(mode_kind), int(leaf_rows), int(prec))
+
+
+def batched_max_leaf_rows(prec: int) -> int:
+    """Longest leaf of a batched-SVD bin at this precision (host query)."""
+    return int(load_library().pylom_svd_batched_max_leaf_rows(int(prec)))
 
 
 class BatchedSVD:

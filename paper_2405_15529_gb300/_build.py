@@ -13,6 +13,7 @@ import shutil
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpylom.so")
@@ -64,5 +65,25 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
+PROBE_SRC = os.path.join(ROOT, "bench_probe.cu")
+PROBE_LIB = os.path.join(ROOT, "bench_probe.so")
+
+
+def build_probe(force: bool = False) -> str:
+    """The benchmark's throughput probes (``bench_probe.cu`` beside bench.py),
+    a library of their own: they are measurement support, not part of the
+    POD library."""
+    if not force and os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= os.path.getmtime(PROBE_SRC):
+        return PROBE_LIB
+    tmp = PROBE_LIB + ".tmp"
+    cmd = [_nvcc(), *ARCH, *FLAGS, "-shared", PROBE_SRC, "-o", tmp, "-lcudart"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on {PROBE_SRC}:\n{r.stderr}")
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
+
+
 if __name__ == "__main__":
     print(build(force=True, verbose=True))
+    print(build_probe(force=True))

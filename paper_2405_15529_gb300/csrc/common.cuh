@@ -94,7 +94,10 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
-__device__ __forceinline__ bool grid_barrier(WsHeader* h, unsigned nblocks) {
+// `expected` is the number of arrivals that releases the barrier (the grid
+// size); limit_ns bounds the wait.
+__device__ __forceinline__ bool grid_barrier(WsHeader* h, unsigned expected,
+                                             unsigned long long limit_ns = kWaitLimitNs) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -103,7 +106,7 @@ __device__ __forceinline__ bool grid_barrier(WsHeader* h, unsigned nblocks) {
       unsigned gen = ld_acquire_u32(&h->barrier_gen);
       __threadfence();
       unsigned arrived = atomicAdd(&h->barrier_count, 1u);
-      if (arrived == nblocks - 1) {
+      if (arrived == expected - 1) {
         atomicExch(&h->barrier_count, 0u);
         __threadfence();
         atomicAdd(&h->barrier_gen, 1u);
@@ -112,7 +115,7 @@ __device__ __forceinline__ bool grid_barrier(WsHeader* h, unsigned nblocks) {
         unsigned polls = 0;
         while (ld_acquire_u32(&h->barrier_gen) == gen) {
           if ((++polls & 63u) == 0) {
-            if (global_ns() - t0 > kWaitLimitNs) {
+            if (global_ns() - t0 > limit_ns) {
               raise_status(h, PYLOM_ERR_TIMEOUT);
               ok = 0;
               break;

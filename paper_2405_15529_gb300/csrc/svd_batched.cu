@@ -1050,6 +1050,11 @@ extern "C" pylom_status pylom_svd_batched_plan(int nbins, const int64_t* N, cons
 
 extern "C" void pylom_svd_batched_plan_destroy(pylom_batched_plan* plan) { delete plan; }
 
+extern "C" int64_t pylom_svd_batched_max_leaf_rows(int prec) {
+  if (prec != PYLOM_PREC_FP64 && prec != PYLOM_PREC_MIXED_3XTF32) return -1;
+  return batched_max_leaf_rows(prec);
+}
+
 extern "C" int64_t pylom_svd_batched_plan_info(const pylom_batched_plan* plan, int bin, int what) {
   if (!plan || bin < 0 || bin >= plan->nbins) return -1;
   switch (what) {

@@ -21,6 +21,13 @@
 //   - The array's device address is looked up once per device with
 //     cudaGetSymbolAddress, the first time this entry point runs with that
 //     device current.  That first call should come before any stream capture.
+//     The address is kept for the life of the process: after a
+//     cudaDeviceReset the module (and the array) is loaded again elsewhere,
+//     so a process that resets a device must not call this entry point
+//     again on it (reload the library instead).
+//   - Every M up to the limit is checked at run time against the layout the
+//     Jacobi kernels carve from the array (header + padded working columns),
+//     so a larger layout is refused rather than overrun.
 //   - Nothing here calls cudaMalloc, cudaFree or an allocating library.
 #include <mutex>
 
@@ -68,13 +75,24 @@ extern "C" pylom_status pylom_svd_small_noalloc(const double* R, int64_t M, int6
     set_error_message("pylom_svd_small_noalloc: max_sweeps must be in [1, %d]", kMaxSweeps);
     return PYLOM_ERR_ARG;
   }
-  static_assert(sizeof(WsHeader) + 2 * sizeof(double) * kNoAllocMaxM * kNoAllocMaxM <= kNoAllocBytes,
-                "scratch must hold the header and both Jacobi arrays");
+  // the layout the Jacobi kernels carve (padded columns, 256-byte aligned
+  // arrays) must fit the fixed array for this M
+  if (sizeof(WsHeader) + svd_state_bytes(M) > kNoAllocBytes) {
+    set_error_message("pylom_svd_small_noalloc: M = %lld needs %zu bytes of scratch, more than the %zu "
+                      "the fixed array holds; use pylom_svd_small with a workspace",
+                      (long long)M, sizeof(WsHeader) + svd_state_bytes(M), kNoAllocBytes);
+    return PYLOM_ERR_SHAPE;
+  }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  if (e != cudaSuccess) {
     set_error_message("pylom_svd_small_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
     return PYLOM_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error_message("pylom_svd_small_noalloc: device index %d is beyond the %d devices this entry "
+                      "point keeps scratch addresses for", dev, kMaxDevices);
+    return PYLOM_ERR_UNSUPPORTED;
   }
   void* base = nullptr;
   {

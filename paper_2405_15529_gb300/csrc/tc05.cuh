@@ -58,16 +58,17 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, int count) {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Wait for phase `parity` of the mbarrier; gives up after kWaitLimitNs and
-// returns false (the caller records PYLOM_ERR_TIMEOUT).
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+// Wait for phase `parity` of the mbarrier; gives up after limit_ns (default
+// kWaitLimitNs) and returns false (the caller records PYLOM_ERR_TIMEOUT).
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
   const unsigned long long t0 = global_ns();
   while (true) {
     uint32_t done;
     asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
                  : "=r"(done) : "r"(smem_u32(mbar)), "r"(parity) : "memory");
     if (done) return true;
-    if (global_ns() - t0 > kWaitLimitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
 }
 

@@ -46,13 +46,26 @@ def _save(d):
     os.replace(tmp, CACHE)
 
 
-def candidates(N: int, Nb: int):
-    # the library splits leaves longer than 1024 rows (512 for complex128)
-    c = sorted({max(Nb, h) for h in (256, 384, 512, 768, 1024)})
-    return [h for h in c if h <= N]
+def set_cache_path(path: str) -> None:
+    """Where the cache lives (default: tune_cache.json beside this file, or
+    $PYLOM_TUNE_CACHE)."""
+    global CACHE
+    CACHE = path
 
 
-def time_leaf_rows(N: int, Nb: int, prec: int, h: int, nbins: int = 8, reps: int = 3, seed: int = 0) -> float:
+CANDIDATE_ROWS = (256, 384, 512, 768, 1024)
+
+
+def candidates(N: int, Nb: int, max_leaf_rows: int):
+    """Distinct leaf heights worth timing for an N x Nb bin: at least Nb
+    rows, at most N, and at most the longest leaf the library runs at this
+    precision (it splits taller hints into more leaves, which would time an
+    already listed configuration again)."""
+    c = sorted({max(Nb, h) for h in CANDIDATE_ROWS})
+    return [h for h in c if h <= N and h <= max_leaf_rows]
+
+
+def time_leaf_rows(N: int, Nb: int, prec: int, h: int, nbins: int = 4, reps: int = 3, seed: int = 0) -> float:
     """Median seconds of one batched run over `nbins` seeded N x Nb bins."""
     import torch
     import synth
@@ -76,20 +89,25 @@ def time_leaf_rows(N: int, Nb: int, prec: int, h: int, nbins: int = 8, reps: int
     return ts[len(ts) // 2]
 
 
-def tune_class(N: int, Nb: int, prec: int) -> int:
-    best, best_t = None, float("inf")
-    for h in candidates(N, Nb):
-        t = time_leaf_rows(N, Nb, prec, h)
-        if t < best_t:
-            best, best_t = h, t
-    return best
+def tune_class(N: int, Nb: int, prec: int):
+    """Times every candidate height on sample bins of this class; returns
+    (fastest height, {height: median seconds})."""
+    times = {}
+    for h in candidates(N, Nb, pg.batched_max_leaf_rows(prec)):
+        times[h] = time_leaf_rows(N, Nb, prec, h)
+    best = min(times, key=lambda h: (times[h], h))
+    return best, times
+
+
+def gpu_name() -> str:
+    import torch
+    return torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
 
 
 def leaf_rows_for(Ns, Nbs, prec: int, tune: bool = False):
     """Leaf heights for a batch (from the cache; missing classes are tuned
     when `tune`, else left to the library's built-in choice, 0)."""
-    import torch
-    gpu = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+    gpu = gpu_name()
     cache = _load()
     out = []
     dirty = False
@@ -97,7 +115,7 @@ def leaf_rows_for(Ns, Nbs, prec: int, tune: bool = False):
         nb_c, n_c = _classes(int(N), int(Nb))
         k = _key(gpu, prec, nb_c, n_c)
         if k not in cache and tune:
-            cache[k] = tune_class(1 << n_c, nb_c, prec)
+            cache[k] = tune_class(1 << n_c, nb_c, prec)[0]
             dirty = True
         h = int(cache.get(k, 0))
         out.append(max(h, int(Nb)) if h else 0)

@@ -130,3 +130,65 @@ def test_batched_rejects_bad_plans():
         pg.BatchedSVD([_dev(synth.spod_bin(200, 129, seed=1))], kmodes=2)     # Nb > 128
     with pytest.raises(pg.PylomError):
         pg.BatchedSVD([_dev(synth.spod_bin(500, 10, seed=1))], kmodes=33)     # kmodes > 32
+
+
+# Bins at the sizes the 256-bin workload runs: Nb up to the 128-column limit,
+# leaves at the 1024-row cap of complex64 leaves (512 for complex128), bins
+# split into several capped leaves, and up to 32 returned modes.  The
+# known-spectrum bins (geometric decay over six decades) keep all 32 leading
+# modes separated, so every mode is compared as a vector.
+_BIG_SPECS = [  # N, Nb, leaf-height hint
+    (4096, 128, 1024),   # 4 leaves of exactly 1024 rows (complex64)
+    (5000, 96, 1024),    # hint 1024 -> 4 leaves of 1250 rows, split to 5 of 1000
+    (3001, 127, 0),      # built-in height, ragged leaves, odd Nb
+    (2048, 64, 1024),
+    (1100, 128, 0),      # split into two leaves of 550 rows
+]
+_BIG_CACHE = {}
+
+
+def _big_bins():
+    if not _BIG_CACHE:
+        for i, (N, Nb, _) in enumerate(_BIG_SPECS):
+            if i % 2 == 0:
+                X, _ = synth.complex_known_spectrum(N, Nb, seeds=(210 + i, 220 + i), dtype=np.complex64)
+            else:
+                X = synth.spod_bin(N, Nb, seed=200 + i)
+            X = np.asfortranarray(X.astype(np.complex64))
+            U_ref, S_ref, _, _ = oracle.zsvd(X.astype(np.complex128))
+            _BIG_CACHE[i] = (X, U_ref, S_ref)
+    return [_BIG_CACHE[i] for i in range(len(_BIG_SPECS))]
+
+
+@pytest.mark.parametrize("kmodes", [8, 32])
+@pytest.mark.parametrize("prec,stol", [(pg.PREC_FP64, FP64_SIGMA), (pg.PREC_MIXED_3XTF32, MIXED_SIGMA)])
+def test_batched_full_size_bins_match_oracle(prec, stol, kmodes):
+    from tests import parity
+    bins = _big_bins()
+    b = pg.BatchedSVD([_dev(X) for X, _, _ in bins], kmodes=kmodes, prec=prec,
+                      leaf_rows=[h for _, _, h in _BIG_SPECS])
+    b.run()
+    assert b.status() == pg.OK
+    hmax = pg.batched_max_leaf_rows(prec)
+    for f, ((X, U_ref, S_ref), (N, Nb, hint)) in enumerate(zip(bins, _BIG_SPECS)):
+        # the leaf partition: the hint (or the cap), split so no leaf exceeds the cap
+        h = hint if hint > 0 else min(hmax, N)
+        P = max(N // h, -(-N // hmax), 1)
+        assert b.info(f, 1) == P, (f, b.info(f, 1), P)
+        assert -(-N // P) <= hmax
+        S = b.S[f].cpu().numpy()
+        assert np.max(np.abs(S - S_ref)) <= stol * S_ref[0], (f, np.max(np.abs(S - S_ref)) / S_ref[0])
+        assert np.all(np.diff(S) <= 0)
+        k = b.k[f]
+        assert k == min(kmodes, Nb)
+        U = b.modes[f].cpu().numpy().astype(np.complex128)
+        floor = 0.0 if prec == pg.PREC_FP64 else MIXED_MODE_FLOOR
+        _check_modes(U, U_ref, S_ref, k, floor=floor)
+        vtol = 1e-5 if prec == pg.PREC_FP64 else 2e-3
+        for grp in parity.clusters(S_ref):
+            if len(grp) == 1 and grp[0] < k and S_ref[grp[0]] >= floor * S_ref[0]:
+                i = grp[0]
+                assert np.linalg.norm(U[:, i] - U_ref[:, i]) <= vtol, (f, i)
+        # orthonormal returned modes (complex64 storage)
+        G = U[:, :k].conj().T @ U[:, :k]
+        assert np.linalg.norm(G - np.eye(k), 2) <= 1e-5

@@ -148,3 +148,18 @@ def test_dmd_graph_replay_is_repeatable():
     torch.cuda.synchronize()
     assert torch.equal(first[0], mu) and torch.equal(first[1], b) and torch.equal(first[2], Phi)
     assert torch.equal(mu[: 4 * K], torch.view_as_real(res.mu).reshape(-1))
+
+
+def test_rank_threshold_matches_oracle():
+    """A singular value of Y1 between (M-1) 2^-52 s_1 and N 2^-52 s_1: the
+    standard threshold max(N, M-1) 2^-52 s_1 drops it on both sides."""
+    N, M = 4000, 9
+    rng = np.random.default_rng(11)
+    Q1, _ = np.linalg.qr(rng.standard_normal((N, 3)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((M - 1, 3)))
+    Y1 = (Q1 * np.array([1.0, 0.5, 1e-14])) @ Q2.T
+    D = np.concatenate([Y1, Y1[:, -1:] * 0.9], axis=1)
+    ref = odmd.dmd(D, remove_mean=False)
+    res = pg.dmd(_dev(D), remove_mean=False, leaf_rows=1000)
+    assert ref["r"] == 2
+    _compare(res, ref)

@@ -175,3 +175,22 @@ def test_pins_catch_planted_mistakes(mutation, monkeypatch):
         except AssertionError:
             failed += 1
     assert failed >= 1, mutation
+
+
+def test_rank_threshold_is_the_standard_rule():
+    """r is cut to the numerical rank of Y1 with the standard threshold for an
+    N x (M-1) matrix, max(N, M-1) * 2^-52 * s_1 (numpy.linalg.matrix_rank's
+    default): a singular value between (M-1) 2^-52 s_1 and N 2^-52 s_1 counts
+    as zero.  The data are built with that value, so the narrower rule would
+    keep one more mode."""
+    N, M = 4000, 9
+    rng = np.random.default_rng(11)
+    Q1, _ = np.linalg.qr(rng.standard_normal((N, 3)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((M - 1, 3)))
+    s = np.array([1.0, 0.5, 1e-14])              # (M-1) eps = 1.8e-15 < 1e-14 < N eps = 8.9e-13
+    Y1 = (Q1 * s) @ Q2.T
+    D = np.concatenate([Y1, Y1[:, -1:] * 0.9], axis=1)
+    assert np.linalg.matrix_rank(Y1) == 2
+    assert np.sum(s > (M - 1) * 2.0 ** -52 * s[0]) == 3
+    out = odmd.dmd(D, remove_mean=False)
+    assert out["r"] == np.linalg.matrix_rank(Y1) == 2
