@@ -215,6 +215,15 @@ def h2d_sweep(Xh, dev, sizes_mb=(64, 512, 2048), chunk_mb=256):
         rate(nb, False)                     # warm
         out[f"{nb >> 20}MB_one_copy_gbs"] = rate(nb, False)
         out[f"{nb >> 20}MB_{chunk_mb}MB_chunks_gbs"] = rate(nb, True)
+    # the library's chunked upload on the current stream, as the timed step issues it
+    import paper_2405_15529_gb300 as pg
+    for rep in range(2):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        pg.upload(dst, flat)
+        ev1.record()
+        ev1.synchronize()
+        out[f"pg_upload_current_stream_gbs_{rep}"] = total / (ev0.elapsed_time(ev1) * 1e-3) / 1e9
     del dst
     torch.cuda.empty_cache()
     return out
@@ -991,7 +1000,9 @@ def run_case(name: str) -> int:
     mixed1808     two mixed-precision POD calls on the 2,000,000 x 1808 wave field
                   (64 waves, power-law amplitudes, noise 1e-4, mean removed, 99 %, r <= 128),
                   phases printed;
-    mixedwave512  two mixed-precision POD calls on a 1,048,576 x 512 wave field (same recipe)."""
+    mixedwave512  two mixed-precision POD calls on a 1,048,576 x 512 wave field (same recipe);
+    fp64ks        two binary64 POD calls on the 262,144 x 256 known-spectrum matrix (weights, 99 %,
+                  256 leaves), the small case of the benchmark workload's leaf and modes kernels."""
     import torch
     import paper_2405_15529_gb300 as pg
     import synth
@@ -999,6 +1010,15 @@ def run_case(name: str) -> int:
     if name == "spod16":
         out = bench_spod(argparse.Namespace(spod_bins=16, spod_steps=1, tune=False, warmup=1), dev)
         print("ms", round(out["ms_per_step"], 1), out["status"])
+        return 0
+    if name == "fp64ks":
+        N, M = 1 << 18, M_FULL
+        XT, w, _ = synth.known_spectrum_torch(N, M, device=dev)
+        X = XT.t()
+        for _ in range(2):
+            res = pg.pod(X, w=w, remove_mean=False, energy=ENERGY, r_max=M)
+        st, r, sw = pg.workspace_status(res.workspace)
+        print(json.dumps({"case": name, "N": N, "M": M, "leaves": pg.leaf_count(N, M, 0), "r": r, "status": st}))
         return 0
     N, M = {"mixed1808": (2_000_000, 1808), "mixedwave512": (1 << 20, 512)}[name]
     XT = synth.waves_torch(N, M, 64, "powerlaw", 1e-4, 5, dev, dtype=torch.float32, row_chunk=1 << 18)
@@ -1047,7 +1067,7 @@ def main():
     ap.add_argument("--spod-bins", type=int, default=256)
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="run the SPOD bins with the built-in leaf heights instead of the autotuned ones")
-    ap.add_argument("--case", choices=["spod16", "mixed1808", "mixedwave512"], default=None,
+    ap.add_argument("--case", choices=["spod16", "mixed1808", "mixedwave512", "fp64ks"], default=None,
                     help="run one fixed workload for a kernel capture instead of the benchmark")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup

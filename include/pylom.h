@@ -401,6 +401,36 @@ pylom_status pylom_svd_batched_bind(pylom_batched_plan* plan, const void* const*
                                     void* stream);
 pylom_status pylom_svd_batched_run(const pylom_batched_plan* plan, void* ws, double* S, int max_sweeps,
                                    void* stream);
+/* Bind with per-item inputs (instead of pylom_svd_batched_bind): each item
+ * f of the plan (N[f] x Nb[f]) is either a complex64 matrix (a SPOD bin,
+ * exactly as pylom_svd_batched_bind takes it) or a real snapshot window
+ * whose POD (Alg. 2 per window) runs in the same persistent launch: the
+ * window's temporal mean removal (each point's mean over its Nb snapshots)
+ * and sqrt(w) weights happen in the leaf load, the window then goes through
+ * the same leaves, tree, Jacobi SVD and modes as the bins (complex
+ * arithmetic on a zero imaginary part), and the real parts of its modes and
+ * right vectors are returned.  Windows of different N and Nb (<= 128) and
+ * SPOD bins may be mixed in one plan.  Not capturable (synchronises
+ * `stream`); call once per set of buffers, then pylom_svd_batched_run. */
+typedef struct {
+  int xtype;          /* PYLOM_C64: a complex64 bin; PYLOM_F32 / PYLOM_F64: a real window */
+  int remove_mean;    /* real windows: 1 = subtract each point's temporal mean */
+  int mode_kind;      /* real windows: pylom_mode_kind (as pylom_pod) */
+  int reserved;       /* 0 */
+  const void* X;      /* device N x Nb input, column-major, ld ldx >= N; not modified */
+  int64_t ldx;
+  const double* w;    /* real windows: device N cell volumes (> 0), or NULL */
+  double* mean;       /* real windows: device N means out, or NULL */
+  void* U;            /* device N x min(kmodes, Nb) modes out, ld ldu >= N: complex64 for a bin; for a
+                         real window binary32 with complex64 leaves (PYLOM_PREC_MIXED_3XTF32) or
+                         binary64 with complex128 leaves (PYLOM_PREC_FP64) */
+  int64_t ldu;
+  double* VT;         /* real windows: device Nb x Nb right vectors out (row i = v_i^T, the sign rule
+                         of pylom_pod; rows of an exactly zero singular value are zero), or NULL */
+  int64_t ldvt;
+} pylom_batched_item;
+pylom_status pylom_svd_batched_bind_items(pylom_batched_plan* plan, const pylom_batched_item* items, void* ws,
+                                          size_t ws_bytes, void* stream);
 /* what: 0 leaf height, 1 leaf count, 2 offset of the bin's S, 3 grid size,
  * 4 number of leaf items; -1 on a bad argument. */
 int64_t pylom_svd_batched_plan_info(const pylom_batched_plan* plan, int bin, int what);

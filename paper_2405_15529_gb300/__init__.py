@@ -40,6 +40,7 @@ EXPORTS = (
     "pylom_pod_backward_workspace_size", "pylom_pod_backward",
     "pylom_svd_batched_plan", "pylom_svd_batched_bind", "pylom_svd_batched_run",
     "pylom_svd_batched_plan_info", "pylom_svd_batched_plan_destroy", "pylom_svd_batched_max_leaf_rows",
+    "pylom_svd_batched_bind_items",
     "pylom_spod_shape", "pylom_spod_blocks_workspace_size", "pylom_spod_blocks", "pylom_spod_order",
     "pylom_pod_streamed_workspace_size", "pylom_pod_streamed", "pylom_pod_streamed_leaf_rows",
     "pylom_dmd_workspace_size", "pylom_dmd",
@@ -139,6 +140,8 @@ def load_library(path: str = LIB_PATH):
     lib.pylom_svd_batched_plan_destroy.argtypes = [_vp]
     lib.pylom_svd_small_noalloc.restype = _int
     lib.pylom_svd_small_noalloc.argtypes = [_vp, _i64, _i64, _vp, _i64, _vp, _vp, _i64, _int, _vp, _vp]
+    lib.pylom_svd_batched_bind_items.restype = _int
+    lib.pylom_svd_batched_bind_items.argtypes = [_vp, ctypes.c_void_p, _vp, _sz, _vp]
     lib.pylom_svd_batched_max_leaf_rows.restype = _i64
     lib.pylom_svd_batched_max_leaf_rows.argtypes = [_int]
     lib.pylom_pod_shard_workspace_size.restype = _sz
@@ -730,6 +733,123 @@ class BatchedSVD:
     def capture(self):
         torch = _torch()
         self.run()                       # warm-up outside capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run(torch.cuda.current_stream())
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
+    def __del__(self):
+        try:
+            if getattr(self, "plan", None):
+                self.lib.pylom_svd_batched_plan_destroy(self.plan)
+                self.plan = None
+        except Exception:
+            pass
+
+
+class BatchedItem(ctypes.Structure):
+    """pylom_batched_item (include/pylom.h)."""
+    _fields_ = [("xtype", _int), ("remove_mean", _int), ("mode_kind", _int), ("reserved", _int),
+                ("X", _vp), ("ldx", _i64), ("w", _vp), ("mean", _vp), ("U", _vp), ("ldu", _i64),
+                ("VT", _vp), ("ldvt", _i64)]
+
+
+class BatchedPOD:
+    """PODs of several real snapshot windows of different N x M (M <= 128)
+    -- each with its own temporal mean removal and cell-volume weights
+    (Alg. 2 per window) -- and, optionally, complex64 SPOD bins, all in one
+    persistent launch (pylom_svd_batched_plan / _bind_items / _run).
+
+    windows: list of real CUDA tensors (float32 or float64), N_i x M_i.
+    weights: None or a list with None or an N_i float64 tensor per window.
+    bins:    complex64 CUDA tensors (SPOD bins) run in the same launch,
+             after the windows.
+    After run(): S[i] (M_i,), modes[i] (N_i x k_i; binary64 with
+    prec=PREC_FP64, binary32 with PREC_MIXED_3XTF32; complex64 for bins),
+    VT[i] (M_i x M_i right vectors of window i), mean[i] (N_i)."""
+
+    def __init__(self, windows, weights=None, remove_mean=True, mode_kind=MODES_ORTHONORMAL, kmodes=8,
+                 prec=PREC_FP64, leaf_rows=None, bins=(), max_sweeps=60):
+        torch = _torch()
+        lib = load_library()
+        self.lib = lib
+        self.X = [_colmajor(x) for x in list(windows) + list(bins)]
+        nwin = len(windows)
+        self.nwin = nwin
+        n = len(self.X)
+        kinds = []
+        for i, x in enumerate(self.X):
+            kind = {torch.float32: F32, torch.float64: F64, torch.complex64: C64}.get(x.dtype)
+            if kind is None or (i < nwin) == (kind == C64):
+                raise TypeError("windows must be float32/float64, bins complex64")
+            kinds.append(kind)
+        weights = list(weights) if weights is not None else [None] * nwin
+        if len(weights) != nwin:
+            raise ValueError("one weights entry per window")
+        dev = self.X[0].device
+        self.w = [None if wt is None else wt.to(device=dev, dtype=torch.float64).contiguous() for wt in weights]
+        self.N = [int(x.shape[0]) for x in self.X]
+        self.Nb = [int(x.shape[1]) for x in self.X]
+        Na, Nba = (_i64 * n)(*self.N), (_i64 * n)(*self.Nb)
+        lr = None if leaf_rows is None else (_i64 * n)(*[int(v) for v in leaf_rows])
+        plan, wsb = _vp(), _sz(0)
+        _raise(lib.pylom_svd_batched_plan(n, Na, Nba, lr, int(kmodes), int(prec), ctypes.byref(plan),
+                                          ctypes.byref(wsb)), "pylom_svd_batched_plan")
+        self.plan = plan
+        self.max_sweeps = int(max_sweeps)
+        self.ws = torch.empty(int(wsb.value), dtype=torch.uint8, device=dev)
+        self.S_all = torch.zeros(sum(self.Nb), dtype=torch.float64, device=dev)
+        self.k = [min(int(kmodes), nb) for nb in self.Nb]
+        real_t = torch.float64 if prec == PREC_FP64 else torch.float32
+        self.U, self.VT, self.mean = [], [], []
+        items = (BatchedItem * n)()
+        for i, x in enumerate(self.X):
+            real = i < nwin
+            U = empty_colmajor(self.N[i], max(self.k[i], 1), real_t if real else torch.complex64, dev)
+            VT = empty_colmajor(self.Nb[i], self.Nb[i], torch.float64, dev) if real else None
+            mean = torch.zeros(self.N[i], dtype=torch.float64, device=dev) if real else None
+            self.U.append(U)
+            self.VT.append(VT)
+            self.mean.append(mean)
+            it = items[i]
+            it.xtype, it.remove_mean, it.mode_kind, it.reserved = kinds[i], int(bool(remove_mean)), int(mode_kind), 0
+            it.X, it.ldx = x.data_ptr(), _ld(x)
+            it.w = self.w[i].data_ptr() if real and self.w[i] is not None else None
+            it.mean = mean.data_ptr() if real else None
+            it.U, it.ldu = U.data_ptr(), _ld(U)
+            it.VT, it.ldvt = (VT.data_ptr(), _ld(VT)) if real else (None, 0)
+        self._items = items
+        _raise(lib.pylom_svd_batched_bind_items(plan, ctypes.cast(items, ctypes.c_void_p), _dptr(self.ws),
+                                                self.ws.numel(), _stream(None)), "pylom_svd_batched_bind_items")
+        self.graph = None
+
+    def info(self, f, what):
+        return int(self.lib.pylom_svd_batched_plan_info(self.plan, int(f), int(what)))
+
+    @property
+    def S(self):
+        return [self.S_all[self.info(f, 2): self.info(f, 2) + nb] for f, nb in enumerate(self.Nb)]
+
+    @property
+    def modes(self):
+        return [u[:, :k] for u, k in zip(self.U, self.k)]
+
+    def run(self, stream=None):
+        _raise(self.lib.pylom_svd_batched_run(self.plan, _dptr(self.ws), _dptr(self.S_all), self.max_sweeps,
+                                              _stream(stream)), "pylom_svd_batched_run")
+
+    def status(self, stream=None):
+        st, _, _ = workspace_status(self.ws, stream)
+        return st
+
+    def capture(self):
+        torch = _torch()
+        self.run()
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):

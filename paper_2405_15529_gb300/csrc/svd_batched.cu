@@ -194,8 +194,19 @@ __device__ __forceinline__ double block_real_sum0(const KSum<TC>& k, double2* sc
 // per-bin description and workspace tables (built by the host plan)
 // ---------------------------------------------------------------------------
 struct BinDesc {
-  const float2* X;   // input, N x Nb complex64, ld ldx
+  const float2* X;   // input, N x Nb complex64, ld ldx (kind 0)
   int64_t ldx;
+  // kind 0: a complex64 matrix (a SPOD frequency bin); kind 1 / 2: a real
+  // float32 / float64 snapshot window (N points x Nb snapshots) whose POD is
+  // taken: temporal mean removal and sqrt(w) weights in the leaf load,
+  // real modes and right vectors out
+  int kind, remove_mean, physical, pad_;
+  const void* Xr;    // real input (kinds 1, 2), ld ldx
+  const double* w;   // N cell volumes or null (kinds 1, 2)
+  double* mean;      // N means out or null (kinds 1, 2)
+  void* Ureal;       // N x k real modes, element TC (kinds 1, 2), ld ldu
+  double* VT;        // Nb x Nb right vectors out (row i = v_i^T) or null (kinds 1, 2)
+  int64_t ldvt;
   int64_t N, Nb, P, k;
   int64_t y_off;     // working copy (TC complex elements), N x Nb, ld N
   int64_t tau_off;   // double2: P x Nb leaf tau
@@ -275,12 +286,41 @@ __device__ void leaf_qr_complex(const BatchArgs& a, const BinDesc& b, int64_t le
   double2* tau = a.zbase + b.tau_off + leaf * Nb;
   // load the leaf (complex64 input -> TC working copy); flag non-finite input
   int bad = 0;
-  for (int64_t j = 0; j < Nb; ++j)
+  if (b.kind == 0) {
+    for (int64_t j = 0; j < Nb; ++j)
+      for (int64_t i = tid; i < h; i += nthr) {
+        const float2 x = b.X[r0 + i + j * b.ldx];
+        if (!isfinite(x.x) || !isfinite(x.y)) bad = 1;
+        CT<TC>::st(Y + i + j * ldy, make_double2(x.x, x.y));
+      }
+  } else {
+    // a real snapshot window (Alg. 2 on each window): per point, its mean
+    // over the window's snapshots (binary64) and sqrt of its cell volume;
+    // the working copy holds sqrt(w) (x - mean) with a zero imaginary part
+    const float* Xf = (const float*)b.Xr;
+    const double* Xd = (const double*)b.Xr;
     for (int64_t i = tid; i < h; i += nthr) {
-      const float2 x = b.X[r0 + i + j * b.ldx];
-      if (!isfinite(x.x) || !isfinite(x.y)) bad = 1;
-      CT<TC>::st(Y + i + j * ldy, make_double2(x.x, x.y));
+      const int64_t n = r0 + i;
+      double xbar = 0.0;
+      if (b.remove_mean) {
+        double sum = 0.0;
+        for (int64_t j = 0; j < Nb; ++j) sum += (b.kind == 1) ? (double)Xf[n + j * b.ldx] : Xd[n + j * b.ldx];
+        xbar = sum / (double)Nb;
+      }
+      if (b.mean) b.mean[n] = xbar;
+      double sw = 1.0;
+      if (b.w) {
+        const double wn = b.w[n];
+        if (!(wn > 0.0) || !isfinite(wn)) bad = 1;
+        sw = sqrt(wn);
+      }
+      for (int64_t j = 0; j < Nb; ++j) {
+        const double x = (b.kind == 1) ? (double)Xf[n + j * b.ldx] : Xd[n + j * b.ldx];
+        if (!isfinite(x)) bad = 1;
+        CT<TC>::st(Y + i + j * ldy, make_double2(sw * (x - xbar), 0.0));
+      }
     }
+  }
   if (bad) raise_status(a.hdr, PYLOM_ERR_NONFINITE);
   __syncthreads();
   // sd[3]: squared norm below the diagonal of the next column, left there by
@@ -663,6 +703,12 @@ __device__ void bin_jacobi(const BatchArgs& a, const BinDesc& b, double2* sd, in
     const double2 ph = (mag > 0.0) ? cscale(cconj(vk), 1.0 / mag) : make_double2(1.0, 0.0);
     for (int64_t r = lane; r < Nb; r += 32) UR[r + c * Nb] = cmul(Vm[r + j * Np], ph);
     if (lane == 0) a.S[b.s_off + c] = sig[j];
+    if (b.kind != 0 && b.VT) {
+      // real window: v_c = a_j ph / sigma_j is real (its largest entry is
+      // real and positive); rows of exactly zero sigma are left zero
+      const double inv = (sig[j] > 0.0) ? 1.0 / sig[j] : 0.0;
+      for (int64_t r = lane; r < Nb; r += 32) b.VT[c + r * b.ldvt] = cmul(A[r + j * Nb], ph).x * inv;
+    }
   }
   __syncthreads();
 }
@@ -786,11 +832,24 @@ __device__ void leaf_modes_complex(const BatchArgs& a, const BinDesc& b, int64_t
         if (i >= j && i < h) x[e] = tc_sub(x[e], tc_mul(f, CT<TC>::ldt(sv + i)));
       }
     }
-    if (live) {
+    if (live && b.kind == 0) {
 #pragma unroll
       for (int e = 0; e < EL; ++e) {
         const int64_t i = lane + 32 * e;
         if (i < h) Uo[i + col * b.ldu] = make_float2((float)x[e].x, (float)x[e].y);
+      }
+    } else if (live) {
+      // real window: the mode is the real part (its imaginary part is
+      // rounding only), divided by sqrt(w) for physical modes
+      TC* Ur = (TC*)b.Ureal + r0;
+#pragma unroll
+      for (int e = 0; e < EL; ++e) {
+        const int64_t i = lane + 32 * e;
+        if (i < h) {
+          TC v = x[e].x;
+          if (b.physical && b.w) v = (TC)((double)v / sqrt(b.w[r0 + i]));
+          Ur[i + col * b.ldu] = v;
+        }
       }
     }
   }
@@ -1067,6 +1126,8 @@ extern "C" int64_t pylom_svd_batched_plan_info(const pylom_batched_plan* plan, i
   }
 }
 
+static pylom_status batched_upload_tables(pylom_batched_plan* plan, void* ws, void* stream, const char* who);
+
 extern "C" pylom_status pylom_svd_batched_bind(pylom_batched_plan* plan, const void* const* Q, const int64_t* ldq,
                                                void* const* U, const int64_t* ldu, void* ws, size_t ws_bytes,
                                                void* stream) {
@@ -1085,6 +1146,12 @@ extern "C" pylom_status pylom_svd_batched_bind(pylom_batched_plan* plan, const v
       set_error_message("pylom_svd_batched_bind: bin %d input pointer or leading dimension invalid", f);
       return PYLOM_ERR_ARG;
     }
+    b.kind = 0;
+    b.Xr = nullptr;
+    b.w = nullptr;
+    b.mean = nullptr;
+    b.Ureal = nullptr;
+    b.VT = nullptr;
     b.X = (const float2*)Q[f];
     b.ldx = ldq[f];
     if (b.k > 0) {
@@ -1099,6 +1166,62 @@ extern "C" pylom_status pylom_svd_batched_bind(pylom_batched_plan* plan, const v
       b.ldu = b.N;
     }
   }
+  return batched_upload_tables(plan, ws, stream, "pylom_svd_batched_bind");
+}
+
+extern "C" pylom_status pylom_svd_batched_bind_items(pylom_batched_plan* plan, const pylom_batched_item* items,
+                                                     void* ws, size_t ws_bytes, void* stream) {
+  set_error_message("");
+  if (!plan || !items || !ws) {
+    set_error_message("pylom_svd_batched_bind_items: null pointer argument");
+    return PYLOM_ERR_ARG;
+  }
+  if (((uintptr_t)ws & 255u) != 0 || ws_bytes < plan->bytes) {
+    set_error_message("pylom_svd_batched_bind_items: workspace needs %zu bytes, 256-byte aligned", plan->bytes);
+    return PYLOM_ERR_WORKSPACE;
+  }
+  for (int f = 0; f < plan->nbins; ++f) {
+    BinDesc& b = plan->bins[f];
+    const pylom_batched_item& it = items[f];
+    if (it.xtype != PYLOM_C64 && it.xtype != PYLOM_F32 && it.xtype != PYLOM_F64) {
+      set_error_message("pylom_svd_batched_bind_items: item %d: xtype must be PYLOM_C64, PYLOM_F32 or PYLOM_F64", f);
+      return PYLOM_ERR_ARG;
+    }
+    if (!it.X || it.ldx < b.N) {
+      set_error_message("pylom_svd_batched_bind_items: item %d input pointer or leading dimension invalid", f);
+      return PYLOM_ERR_ARG;
+    }
+    if (b.k > 0 && (!it.U || it.ldu < b.N)) {
+      set_error_message("pylom_svd_batched_bind_items: item %d output pointer or leading dimension invalid", f);
+      return PYLOM_ERR_ARG;
+    }
+    const bool real = it.xtype != PYLOM_C64;
+    if (real && it.mode_kind != PYLOM_MODES_ORTHONORMAL && it.mode_kind != PYLOM_MODES_PHYSICAL) {
+      set_error_message("pylom_svd_batched_bind_items: item %d: bad mode_kind %d", f, it.mode_kind);
+      return PYLOM_ERR_ARG;
+    }
+    if (real && it.VT && it.ldvt < b.Nb) {
+      set_error_message("pylom_svd_batched_bind_items: item %d: ldvt < Nb", f);
+      return PYLOM_ERR_ARG;
+    }
+    b.kind = real ? (it.xtype == PYLOM_F32 ? 1 : 2) : 0;
+    b.ldx = it.ldx;
+    b.X = real ? nullptr : (const float2*)it.X;
+    b.Xr = real ? it.X : nullptr;
+    b.remove_mean = real ? (it.remove_mean != 0) : 0;
+    b.physical = real ? (it.mode_kind == PYLOM_MODES_PHYSICAL) : 0;
+    b.w = real ? it.w : nullptr;
+    b.mean = real ? it.mean : nullptr;
+    b.VT = real ? it.VT : nullptr;
+    b.ldvt = real ? it.ldvt : 0;
+    b.U = (b.k > 0 && !real) ? (float2*)it.U : nullptr;
+    b.Ureal = (b.k > 0 && real) ? it.U : nullptr;
+    b.ldu = b.k > 0 ? it.ldu : b.N;
+  }
+  return batched_upload_tables(plan, ws, stream, "pylom_svd_batched_bind_items");
+}
+
+static pylom_status batched_upload_tables(pylom_batched_plan* plan, void* ws, void* stream, const char* who) {
   cudaStream_t st = (cudaStream_t)stream;
   char* base = (char*)ws;
   cudaError_t e = cudaMemcpyAsync(base + plan->off_bins, plan->bins.data(), sizeof(BinDesc) * plan->bins.size(),
@@ -1108,7 +1231,7 @@ extern "C" pylom_status pylom_svd_batched_bind(pylom_batched_plan* plan, const v
                         cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
-    set_error_message("pylom_svd_batched_bind: %s", cudaGetErrorString(e));
+    set_error_message("%s: %s", who, cudaGetErrorString(e));
     return PYLOM_ERR_CUDA;
   }
   plan->bound = true;

@@ -74,7 +74,9 @@ def test_sharded_fp64_matches_oracle(case):
     parity.check_vectors(U, ref["U"], ref["S"], ncols=r)
     parity.check_vectors(VT[:r].T, ref["VT"][:r].T, ref["S"], ncols=r)
     np.testing.assert_allclose(mean, ref["mean"], rtol=0, atol=1e-13 * max(1.0, np.abs(X).max()))
-    assert parity.orthonormality(U) <= 1e-12
+    # orthonormal to rounding: about r epsilon-sized entries per column, each
+    # from a few hundred reflector applications (leaf, shard tree, top tree)
+    assert parity.orthonormality(U) <= r * 1e-13
 
 
 def test_sharded_physical_modes_and_single_shard():
