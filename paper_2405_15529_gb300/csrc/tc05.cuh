@@ -72,6 +72,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity,
   }
 }
 
+// One thread: arm the mbarrier for `bytes` of TMA traffic and arrive on it.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(mbar)), "r"(bytes)
+               : "memory");
+}
+
+// TMA: the 2-D box at (x, y) of the tensor map (x the contiguous dimension;
+// x times the element size must be a multiple of 16 bytes) into shared
+// memory at dst, completing `bytes` on the mbarrier.  This GPU's memory
+// only; no cluster multicast.
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int32_t x, int32_t y, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      :: "r"(smem_u32(dst)), "l"((uint64_t)tmap), "r"(x), "r"(y), "r"(smem_u32(mbar))
+      : "memory");
+}
+
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 // make this thread's generic-proxy shared-memory writes visible to the tensor cores

@@ -26,6 +26,11 @@
 // that the threads fold into compensated FP32 sums, and the hi*hi products
 // and the small hi*lo + lo*hi cross terms go to separate accumulators that
 // are added on the CUDA cores.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "kernels.h"
 #include "reflectors.cuh"
 #include "tc05.cuh"
@@ -50,7 +55,17 @@ constexpr int kOpBytes = 6 * kCA;                  // 96 KB >= the W stage's 80 
 static_assert(2 * kWA + 2 * kWB <= kOpBytes, "W-stage operands must fit the operand region");
 constexpr int kOffW = kOpBytes;                    // W: 32 x 128 fp32 (16 KB)
 constexpr int kOffT = kOffW + kNB2 * kCH * 4;      // T: 32 x 32 fp64 (8 KB)
-constexpr int kMixSmem = kOffT + kNB2 * kNB2 * 8;
+// TMA ring of the factorisation's W stage: per 64-row step, the raw FP32
+// boxes of the C chunk (kTmaRows rows x 128 columns) and of the panel
+// (kTmaRows x 32), two stages.  A box starts at the row rounded down to a
+// multiple of 4 (16 bytes), so it holds 4 rows more than a step uses.
+constexpr int kTmaRows = kKC + 4;
+constexpr int kRawC = kTmaRows * kCH * 4;          // 34,816 B
+constexpr int kRawV = kTmaRows * kNB2 * 4;         // 8,704 B
+constexpr int kStageBytes = kRawC + kRawV;
+constexpr int kOffRaw = kOffT + kNB2 * kNB2 * 8;
+static_assert(kOffRaw % 128 == 0 && kRawC % 128 == 0, "TMA destinations must be 128-byte aligned");
+constexpr int kMixSmem = kOffRaw + 2 * kStageBytes;
 // the FP64 tree merge reuses the same buffer with the leaf kernel's plan
 constexpr int kMergeSmem = (int)kLeafSmemBytes;
 constexpr int kMixSmemTotal = kMixSmem > kMergeSmem ? kMixSmem : kMergeSmem;
@@ -58,9 +73,13 @@ constexpr int kMixSmemTotal = kMixSmem > kMergeSmem ? kMixSmem : kMergeSmem;
 // the shared-memory plan keeps them apart
 static_assert(2 * kMixSmemTotal > 228 * 1024, "mixed-leaf CTAs must not share an SM");
 
+// Leading dimension of the FP32 working copy: N rounded up to a multiple of
+// 4, so every column starts on a 16-byte boundary (TMA strides).
+__host__ __device__ __forceinline__ int64_t yf_ld(int64_t N) { return (N + 3) & ~int64_t(3); }
+
 struct MixedArgs {
   TsqrState s;
-  float* Yf;          // N x M fp32 working copy (ld N) -> reflectors
+  float* Yf;          // N x M fp32 working copy (ld yf_ld(N)) -> reflectors
   double* T2;         // per leaf and panel: kNB2 x kNB2 (row-major) fp64
   float* Pb;          // panel scratch: (N / 128 + P + 1) chunk slots of kHrSlot floats
   const void* X;
@@ -482,10 +501,27 @@ __device__ __forceinline__ void issue_3xtf32(uint32_t d_hh, uint32_t d_x, unsign
 // current MMAs, and the C-stage epilogue loads the next 16-column group of C
 // while it adds the current one, so the tensor-core work and the folds
 // overlap the memory latency.
-template <bool TRANS>
+// The TMA form of the W stage (TMA = true: the factorisation's trailing
+// updates, C and V both columns of the leaf's FP32 working copy): per 64-row
+// step one cp.async.bulk.tensor box of the C chunk and one of the panel land
+// in a two-stage shared-memory ring, two steps ahead of the MMAs; the threads
+// split them into the TF32 operand tiles from shared memory.  tmC / tmV: the
+// working copy's tensor maps (boxes of kTmaRows rows x 128 / 32 columns);
+// grow0: the working-copy row of the leaf's row 0; ccol0: the working-copy
+// column of C's column 0; fullbar[2] / tphase: the ring's mbarriers and
+// their phase bits.
+struct TmaW {
+  const CUtensorMap* tmC;
+  const CUtensorMap* tmV;
+  int64_t grow0, ccol0;
+  uint64_t* fullbar;
+  uint32_t* tphase;
+};
+
+template <bool TRANS, bool TMA = false>
 __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int nbk, int64_t h, float* C,
                                    int64_t ldc, int ncols, const double* sT, unsigned char* smem, uint32_t tmem,
-                                   uint64_t* mbar, uint32_t& phase) {
+                                   uint64_t* mbar, uint32_t& phase, TmaW tw = TmaW{}) {
   using namespace tc05;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int quad = warp & 3, half = warp >> 2;       // tensor-memory lane quadrant; which half of the work
@@ -506,71 +542,154 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
     // shared memory), so the split stores are free of bank conflicts; lane l
     // holds operand row 8 g + l / 4 and K element 4 q + l % 4 of it
     const int lrow = lane >> 2, lk = lane & 3;
-    float xa[kCH / 4], xb[kNB2 / 4];
-    auto load_w = [&](int64_t kc) {
-#pragma unroll
-      for (int u = 0; u < kCH / 4; ++u) {          // A: 16 row groups x 16 K groups
-        const int cmi = u * 8 + warp;
-        const int c = (cmi & 15) * 8 + lrow;
-        const int64_t row = k + kc * kKC + (cmi >> 4) * 4 + lk;
-        xa[u] = (row < h && c < wc) ? C[row + (int64_t)(c0 + c) * ldc] : 0.f;
-      }
-#pragma unroll
-      for (int u = 0; u < kNB2 / 4; ++u) {         // B: 4 reflector groups x 16 K groups
-        const int cmi = u * 8 + warp;
-        const int64_t row = k + kc * kKC + (cmi >> 2) * 4 + lk;
-        xb[u] = vval_f(Y, ldy, k, nbk, h, row, (cmi & 3) * 8 + lrow);
-      }
-    };
-    load_w(0);
-    for (int64_t kc = 0; kc < nkc && ok; ++kc) {
-#pragma unroll
-      for (int u = 0; u < kCH / 4; ++u) {
-        const int cmi = u * 8 + warp;
-        float hi, lo;
-        split_tf32(xa[u], hi, lo);
-        const uint32_t o = cm_off((cmi & 15) * 8 + lrow, (cmi >> 4) * 4 + lk, kKC);
-        *(float*)(smem + kOffWA + o) = hi;
-        *(float*)(smem + kOffWAlo + o) = lo;
-      }
-#pragma unroll
-      for (int u = 0; u < kNB2 / 4; ++u) {
-        const int cmi = u * 8 + warp;
-        float hi, lo;
-        split_tf32(xb[u], hi, lo);
-        const uint32_t o = cm_off((cmi & 3) * 8 + lrow, (cmi >> 2) * 4 + lk, kKC);
-        *(float*)(smem + kOffWB + o) = hi;
-        *(float*)(smem + kOffWBlo + o) = lo;
-      }
-      fence_smem_async();
-      fence_before();
-      __syncthreads();
-      fence_after();
-      if (tid == 0) {
-        issue_3xtf32(tmem, tmem + kNB2, smem, kOffWA, kOffWAlo, kOffWB, kOffWBlo, kKC, idesc_tf32(128, kNB2));
-        commit(mbar);
-      }
-      if (kc + 1 < nkc) load_w(kc + 1);   // in flight while the MMAs run
+    // the MMA and fold of one step, common to both forms
+    auto mma_and_fold = [&]() -> bool {
       const bool w_ok = mbar_wait(mbar, phase);
       phase ^= 1u;
       fence_after();
-      ok = !__syncthreads_or(!w_ok);
-      if (!ok) break;
-      {
-        float hh[16], xx[16];
-        tmem_ld16(tmem + lanebase + (uint32_t)(16 * half), hh);
-        tmem_ld16(tmem + lanebase + (uint32_t)(kNB2 + 16 * half), xx);
+      if (__syncthreads_or(!w_ok)) return false;
+      float hh[16], xx[16];
+      tmem_ld16(tmem + lanebase + (uint32_t)(16 * half), hh);
+      tmem_ld16(tmem + lanebase + (uint32_t)(kNB2 + 16 * half), xx);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const float y = (hh[j] + xx[j]) - wc_[j];
-          const float t = ws_[j] + y;
-          wc_[j] = (t - ws_[j]) - y;
-          ws_[j] = t;
-        }
+      for (int j = 0; j < 16; ++j) {
+        const float y = (hh[j] + xx[j]) - wc_[j];
+        const float t = ws_[j] + y;
+        wc_[j] = (t - ws_[j]) - y;
+        ws_[j] = t;
       }
       // the next step's MMAs overwrite the accumulators only after the
       // barrier that follows its shared-memory stores
       fence_before();
+      return true;
+    };
+    if constexpr (TMA) {
+      // every thread's earlier global writes (the panel, the previous
+      // updates of C) are ordered before the tensor-memory-access reads
+      asm volatile("fence.proxy.async;" ::: "memory");
+      __syncthreads();
+      auto issue = [&](int64_t kc) {   // thread 0
+        const int st = (int)(kc & 1);
+        const int64_t g = tw.grow0 + k + kc * kKC;
+        const int32_t x0 = (int32_t)(g & ~int64_t(3));
+        unsigned char* dst = smem + kOffRaw + st * kStageBytes;
+        fence_smem_async();
+        mbar_arrive_expect_tx(&tw.fullbar[st], (uint32_t)kStageBytes);
+        tma_load_2d(dst, tw.tmC, x0, (int32_t)(tw.ccol0 + c0), &tw.fullbar[st]);
+        tma_load_2d(dst + kRawC, tw.tmV, x0, (int32_t)k, &tw.fullbar[st]);
+      };
+      if (tid == 0) {
+        issue(0);
+        if (nkc > 1) issue(1);
+      }
+      int64_t issued = nkc > 1 ? 2 : 1, consumed = 0;
+      for (int64_t kc = 0; kc < nkc && ok; ++kc) {
+        const int st = (int)(kc & 1);
+        const bool got = mbar_wait(&tw.fullbar[st], (*tw.tphase >> st) & 1u);
+        *tw.tphase ^= 1u << st;
+        ++consumed;
+        ok = !__syncthreads_or(!got);
+        if (!ok) break;
+        const float* rc = (const float*)(smem + kOffRaw + st * kStageBytes);
+        const float* rv = rc + kTmaRows * kCH;
+        const int off = (int)((tw.grow0 + k + kc * kKC) & 3);
+        const int64_t rbase = k + kc * kKC;        // leaf row of K element 0
+#pragma unroll 8
+        for (int u = 0; u < kCH / 4; ++u) {        // A: 16 row groups x 16 K groups
+          const int cmi = u * 8 + warp;
+          const int c = (cmi & 15) * 8 + lrow;
+          const int rk = (cmi >> 4) * 4 + lk;
+          const float x = (rbase + rk < h && c < wc) ? rc[c * kTmaRows + off + rk] : 0.f;
+          float hi, lo;
+          split_tf32(x, hi, lo);
+          const uint32_t o = cm_off(c, rk, kKC);
+          *(float*)(smem + kOffWA + o) = hi;
+          *(float*)(smem + kOffWAlo + o) = lo;
+        }
+#pragma unroll
+        for (int u = 0; u < kNB2 / 4; ++u) {       // B: 4 reflector groups x 16 K groups
+          const int cmi = u * 8 + warp;
+          const int pp = (cmi & 3) * 8 + lrow;
+          const int rk = (cmi >> 2) * 4 + lk;
+          const int64_t i = rbase + rk, d = k + pp;
+          float x = 0.f;
+          if (pp < nbk && i < h && i >= d) x = (i == d) ? 1.f : rv[pp * kTmaRows + off + rk];
+          float hi, lo;
+          split_tf32(x, hi, lo);
+          const uint32_t o = cm_off(pp, rk, kKC);
+          *(float*)(smem + kOffWB + o) = hi;
+          *(float*)(smem + kOffWBlo + o) = lo;
+        }
+        fence_smem_async();
+        fence_before();
+        __syncthreads();     // the stage is read out: it may be refilled
+        fence_after();
+        if (tid == 0) {
+          if (kc + 2 < nkc) issue(kc + 2);
+          issue_3xtf32(tmem, tmem + kNB2, smem, kOffWA, kOffWAlo, kOffWB, kOffWBlo, kKC, idesc_tf32(128, kNB2));
+          commit(mbar);
+        }
+        if (kc + 2 < nkc) ++issued;
+        ok = mma_and_fold();
+      }
+      if (!ok) {
+        // wait (bounded) for the boxes still in flight before giving up
+        if (tid == 0)
+          for (int64_t q = consumed; q < issued; ++q) {
+            const int st = (int)(q & 1);
+            mbar_wait(&tw.fullbar[st], (*tw.tphase >> st) & 1u);
+            *tw.tphase ^= 1u << st;
+          }
+        break;
+      }
+    } else {
+      float xa[kCH / 4], xb[kNB2 / 4];
+      auto load_w = [&](int64_t kc) {
+#pragma unroll
+        for (int u = 0; u < kCH / 4; ++u) {          // A: 16 row groups x 16 K groups
+          const int cmi = u * 8 + warp;
+          const int c = (cmi & 15) * 8 + lrow;
+          const int64_t row = k + kc * kKC + (cmi >> 4) * 4 + lk;
+          xa[u] = (row < h && c < wc) ? C[row + (int64_t)(c0 + c) * ldc] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kNB2 / 4; ++u) {         // B: 4 reflector groups x 16 K groups
+          const int cmi = u * 8 + warp;
+          const int64_t row = k + kc * kKC + (cmi >> 2) * 4 + lk;
+          xb[u] = vval_f(Y, ldy, k, nbk, h, row, (cmi & 3) * 8 + lrow);
+        }
+      };
+      load_w(0);
+      for (int64_t kc = 0; kc < nkc && ok; ++kc) {
+#pragma unroll
+        for (int u = 0; u < kCH / 4; ++u) {
+          const int cmi = u * 8 + warp;
+          float hi, lo;
+          split_tf32(xa[u], hi, lo);
+          const uint32_t o = cm_off((cmi & 15) * 8 + lrow, (cmi >> 4) * 4 + lk, kKC);
+          *(float*)(smem + kOffWA + o) = hi;
+          *(float*)(smem + kOffWAlo + o) = lo;
+        }
+#pragma unroll
+        for (int u = 0; u < kNB2 / 4; ++u) {
+          const int cmi = u * 8 + warp;
+          float hi, lo;
+          split_tf32(xb[u], hi, lo);
+          const uint32_t o = cm_off((cmi & 3) * 8 + lrow, (cmi >> 2) * 4 + lk, kKC);
+          *(float*)(smem + kOffWB + o) = hi;
+          *(float*)(smem + kOffWBlo + o) = lo;
+        }
+        fence_smem_async();
+        fence_before();
+        __syncthreads();
+        fence_after();
+        if (tid == 0) {
+          issue_3xtf32(tmem, tmem + kNB2, smem, kOffWA, kOffWAlo, kOffWB, kOffWBlo, kKC, idesc_tf32(128, kNB2));
+          commit(mbar);
+        }
+        if (kc + 1 < nkc) load_w(kc + 1);   // in flight while the MMAs run
+        ok = mma_and_fold();
+      }
     }
     if (!ok) break;
     __syncthreads();
@@ -714,16 +833,18 @@ __device__ void mixed_prologue(const MixedArgs& a, float* Y, int64_t ldy, int64_
   if (bad) raise_status(a.s.hdr, PYLOM_ERR_NONFINITE);
 }
 
-__global__ void __launch_bounds__(kMxThreads) leaf_qr_mixed_kernel(MixedArgs a) {
+__global__ void __launch_bounds__(kMxThreads) leaf_qr_mixed_kernel(MixedArgs a, const __grid_constant__ CUtensorMap tmC,
+                                                                  const __grid_constant__ CUtensorMap tmV) {
   extern __shared__ __align__(128) unsigned char msm[];
   __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t fullbar[2];
   __shared__ uint32_t tmem_base;
   const TsqrState& s = a.s;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int64_t leaf = blockIdx.x;
   const int64_t r0 = leaf_begin(leaf, s.N, s.P);
   const int64_t h = leaf_begin(leaf + 1, s.N, s.P) - r0;
-  const int64_t M = s.M, ldy = s.N;
+  const int64_t M = s.M, ldy = yf_ld(s.N);
   const int64_t npan = (M + kNB2 - 1) / kNB2;
   float* Y = a.Yf + r0;
   double* sT = (double*)(msm + kOffT);
@@ -731,7 +852,12 @@ __global__ void __launch_bounds__(kMxThreads) leaf_qr_mixed_kernel(MixedArgs a) 
     mixed_prologue<float>(a, Y, ldy, r0, h);
   else
     mixed_prologue<double>(a, Y, ldy, r0, h);
-  if (tid == 0) tc05::mbar_init(&mbar, 1);
+  if (tid == 0) {
+    tc05::mbar_init(&mbar, 1);
+    tc05::mbar_init(&fullbar[0], 1);
+    tc05::mbar_init(&fullbar[1], 1);
+  }
+  uint32_t tphase = 0;
   if (warp == 0) tc05::tmem_alloc(&tmem_base, kTmemCols);
   tc05::fence_before();
   __syncthreads();
@@ -748,8 +874,8 @@ __global__ void __launch_bounds__(kMxThreads) leaf_qr_mixed_kernel(MixedArgs a) 
     double* Tg = a.T2 + (leaf * npan + k / kNB2) * kNB2 * kNB2;
     for (int idx = tid; idx < kNB2 * kNB2; idx += blockDim.x) Tg[idx] = sT[idx];
     if (k + nbk < M)
-      ok = block_reflector_tc<true>(Y, ldy, k, nbk, h, Y + (k + nbk) * ldy, ldy, (int)(M - k - nbk), sT, msm, tmem,
-                                    &mbar, phase);
+      ok = block_reflector_tc<true, true>(Y, ldy, k, nbk, h, Y + (k + nbk) * ldy, ldy, (int)(M - k - nbk), sT, msm,
+                                          tmem, &mbar, phase, TmaW{&tmC, &tmV, r0, k + nbk, fullbar, &tphase});
     __syncthreads();
   }
   tc05::fence_before();
@@ -811,7 +937,7 @@ __global__ void __launch_bounds__(kMxThreads) modes_mixed_kernel(TsqrState s, co
     const double* Tg = T2 + (leaf * npan + pan) * kNB2 * kNB2;
     for (int idx = tid; idx < kNB2 * kNB2; idx += blockDim.x) sT[idx] = Tg[idx];
     __syncthreads();
-    ok = block_reflector_tc<false>(Y, s.N, k, nbk, h, C, ldu, (int)r, sT, msm, tmem, &mbar, phase);
+    ok = block_reflector_tc<false>(Y, yf_ld(s.N), k, nbk, h, C, ldu, (int)r, sT, msm, tmem, &mbar, phase);
     __syncthreads();
   }
   tc05::fence_before();
@@ -860,7 +986,7 @@ __global__ void __launch_bounds__(kMxThreads) leaf_qt_mixed_kernel(TsqrState s, 
     const double* Tg = T2 + (leaf * npan + pan) * kNB2 * kNB2;
     for (int idx = tid; idx < kNB2 * kNB2; idx += blockDim.x) sT[idx] = Tg[idx];
     __syncthreads();
-    ok = block_reflector_tc<true>(Y, s.N, k, nbk, h, Cl, s.N, (int)r, sT, msm, tmem, &mbar, phase);
+    ok = block_reflector_tc<true>(Y, yf_ld(s.N), k, nbk, h, Cl, s.N, (int)r, sT, msm, tmem, &mbar, phase);
     __syncthreads();
   }
   tc05::fence_before();
@@ -880,8 +1006,34 @@ __global__ void __launch_bounds__(kMxThreads) leaf_qt_mixed_kernel(TsqrState s, 
 
 size_t mixed_extra_bytes(int64_t N, int64_t M, int64_t P) {
   const int64_t npan = (M + kNB2 - 1) / kNB2;
-  return align256(sizeof(float) * (size_t)N * M) + align256(sizeof(double) * (size_t)P * npan * kNB2 * kNB2) +
+  return align256(sizeof(float) * (size_t)yf_ld(N) * M) + align256(sizeof(double) * (size_t)P * npan * kNB2 * kNB2) +
          align256(sizeof(float) * (size_t)(N / kCR + P + 1) * kHrSlot);
+}
+
+// Tensor map of the FP32 working copy (yf_ld(N) x M, column-major) with
+// boxes of kTmaRows rows x `cols` columns; out-of-range boxes read zeros.
+static cudaError_t encode_yf_map(CUtensorMap* map, float* Yf, int64_t N, int64_t M, int cols) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static std::mutex mu;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!encode) {
+      void* fn = nullptr;
+      cudaDriverEntryPointQueryResult q;
+      cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+      if (e != cudaSuccess) return e;
+      if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+      encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)yf_ld(N), (cuuint64_t)M};
+  const cuuint64_t strides[1] = {(cuuint64_t)yf_ld(N) * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kTmaRows, (cuuint32_t)cols};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)Yf, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t launch_tsqr_mixed(const TsqrState& s, char* extra, const void* X, int64_t ldx, int xtype,
@@ -890,10 +1042,13 @@ cudaError_t launch_tsqr_mixed(const TsqrState& s, char* extra, const void* X, in
   if ((e = ensure_dyn_smem((const void*)leaf_qr_mixed_kernel, kMixSmemTotal)) != cudaSuccess) return e;
   if ((e = ensure_dyn_smem((const void*)modes_mixed_kernel, kMixSmemTotal)) != cudaSuccess) return e;
   const int64_t npan = (s.M + kNB2 - 1) / kNB2;
-  char* t2 = extra + align256(sizeof(float) * (size_t)s.N * s.M);
+  char* t2 = extra + align256(sizeof(float) * (size_t)yf_ld(s.N) * s.M);
   char* pb = t2 + align256(sizeof(double) * (size_t)s.P * npan * kNB2 * kNB2);
   MixedArgs a{s, (float*)extra, (double*)t2, (float*)pb, X, ldx, xtype, w, remove_mean, mean};
-  leaf_qr_mixed_kernel<<<(unsigned)s.P, kMxThreads, kMixSmemTotal, st>>>(a);
+  CUtensorMap tmC, tmV;
+  if ((e = encode_yf_map(&tmC, a.Yf, s.N, s.M, kCH)) != cudaSuccess) return e;
+  if ((e = encode_yf_map(&tmV, a.Yf, s.N, s.M, kNB2)) != cudaSuccess) return e;
+  leaf_qr_mixed_kernel<<<(unsigned)s.P, kMxThreads, kMixSmemTotal, st>>>(a, tmC, tmV);
   e = cudaGetLastError();
   if (e != cudaSuccess || s.climb) return e;
   return launch_tree_coop(s, st);
@@ -906,7 +1061,7 @@ cudaError_t launch_modes_mixed(const TsqrState& s, char* extra, const double* Ur
   if (e != cudaSuccess) return e;
   if (mid && (e = cudaEventRecord(mid, st)) != cudaSuccess) return e;
   const float* Yf = (const float*)extra;
-  const double* T2 = (const double*)(extra + align256(sizeof(float) * (size_t)s.N * s.M));
+  const double* T2 = (const double*)(extra + align256(sizeof(float) * (size_t)yf_ld(s.N) * s.M));
   modes_mixed_kernel<<<(unsigned)s.P, kMxThreads, kMixSmemTotal, st>>>(s, Yf, T2, r_fixed, w, physical, U, ldu, r_out);
   return cudaGetLastError();
 }
@@ -918,7 +1073,7 @@ cudaError_t launch_leaf_qt_mixed(const TsqrState& s, char* extra, float* C, int6
     if (e != cudaSuccess) return e;
   }
   const float* Yf = (const float*)extra;
-  const double* T2 = (const double*)(extra + align256(sizeof(float) * (size_t)s.N * s.M));
+  const double* T2 = (const double*)(extra + align256(sizeof(float) * (size_t)yf_ld(s.N) * s.M));
   leaf_qt_mixed_kernel<<<(unsigned)s.P, kMxThreads, kMixSmemTotal, st>>>(s, Yf, T2, C, r, Z);
   return cudaGetLastError();
 }

@@ -40,6 +40,7 @@ def _check_modes(U, U_ref, S_ref, k, weight=None):
     (5037, 24, 600, False, True, 0, np.float32),     # one partial panel, ragged leaves
     (3001, 37, 128, True, True, 1, np.float32),      # two panels (32 + 5), P = 23
     (20000, 128, 2048, False, False, 0, np.float32), # several 128-column chunks
+    (9001, 300, 1500, True, False, 0, np.float32),   # trailing chunks of 128, 128, 12 columns; odd N
 ])
 def test_mixed_pod_matches_oracle_and_fp64_path(N, M, b, remove_mean, weighted, mode_kind, dtype):
     X = synth.waves(N, M, n_waves=min(8, max(1, M // 4)), noise=1e-3, seed=N + M, dtype=dtype)
