@@ -323,7 +323,11 @@ def bench_mixed(args, dev):
     XT, w, s = synth.known_spectrum_torch(N, M, device=dev, dtype=torch.float32)
     X = XT.t()
     prec = pg.PREC_MIXED_3XTF32
-    ws = torch.empty(pg.pod_workspace_size(N, M, 0, M, pg.F32, prec), dtype=torch.uint8, device=dev)
+    leaf = 0
+    if args.tune:
+        from paper_2405_15529_gb300 import tune
+        leaf = tune.pod_leaf_rows_for(N, M, prec, tune=True)
+    ws = torch.empty(pg.pod_workspace_size(N, M, leaf, M, pg.F32, prec), dtype=torch.uint8, device=dev)
     U = pg.empty_colmajor(N, M, torch.float32, dev)
     S = torch.empty(M, dtype=torch.float64, device=dev)
     VT = pg.empty_colmajor(M, M, torch.float64, dev)
@@ -331,7 +335,8 @@ def bench_mixed(args, dev):
     out = (U, S, VT, None, r_dev)
 
     def step():
-        pg.pod(X, w=w, remove_mean=False, energy=ENERGY, r_max=M, prec=prec, workspace=ws, out=out, check=False)
+        pg.pod(X, w=w, remove_mean=False, energy=ENERGY, r_max=M, prec=prec, leaf_rows=leaf, workspace=ws, out=out,
+               check=False)
 
     for _ in range(args.warmup):
         step()
@@ -356,6 +361,7 @@ def bench_mixed(args, dev):
     S64 = ref.S.cpu().numpy()
     leaf_ms = phases["leaf_qr_tree"] / max(n, 1)
     out = {"workload": f"known_spectrum_{N}x{M}_f32_weighted_energy0.99", "status": st, "r": r,
+           "leaf_rows": leaf, "leaves": pg.leaf_count(N, M, leaf) if leaf else min(152, pg.leaf_count(N, M, 0)),
            "ms_per_step": ms, "value": N * M * 4 / (ms * 1e-3) / 1e9, "unit": "GB/s of X (float32)",
            "phases_ms_per_step": {k: v / max(n, 1) for k, v in phases.items()},
            "fp64_path_ms_same_x": ms64, "speedup_vs_fp64_path": ms64 / ms,
@@ -803,6 +809,14 @@ def run_ours(args, rank, world, local_rank):
     XT, w, s = synth.known_spectrum_torch(N, M, device=dev)
     X = XT.t()
     torch.cuda.synchronize()
+    # leaf height: given, or the autotuner's (timed outside the timed region, cached)
+    tuned_leaf = None
+    if args.leaf_rows == 0 and args.tune:
+        from paper_2405_15529_gb300 import tune
+        t_tune = time.perf_counter()
+        tuned_leaf = tune.pod_leaf_rows_for(N, M, pg.PREC_FP64, tune=True)
+        t_tune = time.perf_counter() - t_tune
+        args.leaf_rows = tuned_leaf
     P = pg.leaf_count(N, M, args.leaf_rows)
     ws_bytes = pg.pod_workspace_size(N, M, args.leaf_rows, M, pg.F64, pg.PREC_FP64)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
@@ -970,6 +984,10 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N, "M": M, "leaves": P, "r": r,
+                       "leaf_rows": args.leaf_rows,
+                       "leaf_rows_source": ("autotuned (tune.pod_leaf_rows_for, %.0f s outside the timed region)"
+                                            % t_tune) if tuned_leaf else (
+                           "given" if args.leaf_rows else "automatic"),
                        "l2": "inputs (8.6 GB per rank) larger than L2 (129 MB); no flush",
                        "parallelism": f"independent problems x{world}"},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_mma, "unit": "TFLOP/s",

@@ -87,11 +87,11 @@ const char* pylom_last_error(void);
 int64_t pylom_leaf_count(int64_t N, int64_t M, int64_t leaf_rows);
 
 /* Tree reduction of the leaf R factors (Sec. 3.1, the reduce loop of
- * Alg. 1), used by pylom_pod and pylom_tsqr.  Below 384 columns the leaf
- * kernels merge pairs as they finish (the second block to reach a merge
- * performs it); from 384 columns on, one cooperative launch after the
- * leaves spreads every merge of a level over all thread blocks, one panel
- * of 16 columns per grid-wide step.  Both leave the same pairing, merged R
+ * Alg. 1), used by pylom_pod and pylom_tsqr.  Below 384 columns and 64
+ * leaves the leaf kernels merge pairs as they finish (the second block to
+ * reach a merge performs it); from 384 columns or 64 leaves on, one
+ * cooperative launch after the leaves spreads every merge of a level over
+ * all thread blocks, one panel of 16 columns per grid-wide step.  Both leave the same pairing, merged R
  * and node reflectors.  The environment variable PYLOM_TREE = "climb" or
  * "coop", read at each call, forces one form (testing and tuning). */
 

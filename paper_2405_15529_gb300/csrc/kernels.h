@@ -9,8 +9,10 @@ namespace pylom {
 
 // Householder panel width of the FP64 leaf QR (two 8-row DMMA tiles).
 constexpr int kNB = 16;
-// From this many columns on, the tree merges run in tree_coop_kernel.
+// From this many columns, or this many leaves, on, the tree merges run in
+// tree_coop_kernel.
 constexpr int64_t kCoopTreeMinM = 384;
+constexpr int64_t kCoopTreeMinP = 64;
 bool use_climb_tree(int64_t M, int64_t P);
 
 // Device pointers of one TSQR (+ modes) problem, carved from a workspace.

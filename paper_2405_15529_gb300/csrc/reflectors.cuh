@@ -263,6 +263,146 @@ static __device__ void merge_panel_factor(double* Rt, double* Rb, int64_t M, int
   }
 }
 
+// The same panel factorisation with the panel staged in shared memory: the
+// bottom rows 0 .. k+nbk-1 of the panel columns of Rb and the kNB x kNB top
+// block of Rt are loaded once, the column steps run from shared memory (no
+// L2 round trip per column) on four warps -- one per SM sub-partition, so
+// the panel's FP64 FMAs use every FP64 unit of the SM -- synchronised by a
+// 128-thread named barrier three times per column, and the panel is written
+// back.  The arithmetic is the column sweep above, term for term; only the
+// order of the partial sums differs.  The other warps of the block wait.
+// sP: (k + nbk) * kNB + kNB * kNB + kMergeStageExtra doubles of shared memory.
+constexpr int kMergeStageExtra = kNB + 4 * kNB + 4 + 4;
+constexpr int kMergeStageThreads = 128;
+constexpr int64_t kMergeStageDoubles = 2 * kSmW;   // the sW / sWp buffers, free while a panel is factored
+__host__ __device__ constexpr bool merge_panel_staged(int64_t M) {
+  return M * kNB + kNB * kNB + kMergeStageExtra <= kMergeStageDoubles;
+}
+
+__device__ __forceinline__ void stage_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+static __device__ void merge_panel_factor_staged(double* Rt, double* Rb, int64_t M, int64_t k, int nbk,
+                                                 double* tau_out, double* sT, double* sP) {
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NT = kMergeStageThreads;
+  const int64_t nr = k + nbk;
+  double* Pb = sP;               // Pb[i + q nr] = Rb[i, k + q], rows 0 .. nr-1
+  double* Pt = sP + nr * kNB;    // Pt[r + q kNB] = Rt[k + r, k + q]
+  double* Pd = Pt + kNB * kNB;   // the column step's dot products, for the T recurrence
+  double* red = Pd + kNB;        // per-warp partial dot products (4 x kNB)
+  double* red2 = red + 4 * kNB;  // per-warp partial norms
+  double* sc = red2 + 4;         // tau, beta, scale of the current column
+  for (int64_t idx = tid; idx < nr * nbk; idx += nthr) {
+    const int64_t i = idx % nr, q = idx / nr;
+    Pb[i + q * nr] = ldcg(Rb + i + (k + q) * M);
+  }
+  for (int idx = tid; idx < nbk * nbk; idx += nthr) {
+    const int r = idx % nbk, q = idx / nbk;
+    Pt[r + q * kNB] = ldcg(Rt + (k + r) + (k + q) * M);
+  }
+  __syncthreads();
+  if (tid < NT) {
+    double nx = 0.0;
+    for (int64_t i = tid; i <= k; i += NT) nx += Pb[i] * Pb[i];
+    nx = warp_sum(nx);
+    if (lane == 0) red2[warp] = nx;
+    stage_bar();
+    double xx = red2[0] + red2[1] + red2[2] + red2[3];
+    for (int jj = 0; jj < nbk; ++jj) {
+      const int64_t c = k + jj;
+      // thread 0 forms the reflector's scalars (FP64 square roots and
+      // divisions are slow on this part) and shares them
+      if (tid == 0) {
+        const double alpha = Pt[jj + jj * kNB];
+        double tau0 = 0.0, beta0 = alpha, scale0 = 0.0;
+        if (xx != 0.0) {
+          const double nrm = sqrt(alpha * alpha + xx);
+          beta0 = (alpha >= 0.0) ? -nrm : nrm;
+          tau0 = (beta0 - alpha) / beta0;
+          scale0 = 1.0 / (alpha - beta0);
+        }
+        sc[0] = tau0;
+        sc[1] = beta0;
+        sc[2] = scale0;
+      }
+      stage_bar();
+      const double tau_c = sc[0], beta = sc[1], scale = sc[2];
+      // pass A: u_c = scale * bottom column c; dots with the other panel columns
+      double acc[kNB];
+#pragma unroll
+      for (int q = 0; q < kNB; ++q) acc[q] = 0.0;
+      for (int64_t i = tid; i <= c; i += NT) {
+        const double u = Pb[i + jj * nr] * scale;
+        Pb[i + jj * nr] = u;
+#pragma unroll
+        for (int q = 0; q < kNB; ++q)
+          if (q < nbk && q != jj) acc[q] += u * Pb[i + q * nr];
+      }
+#pragma unroll
+      for (int q = 0; q < kNB; ++q) {
+        const double v = warp_sum(acc[q]);
+        if (lane == 0) red[warp * kNB + q] = v;
+      }
+      stage_bar();
+      double d[kNB];
+#pragma unroll
+      for (int q = 0; q < kNB; ++q) {
+        acc[q] = (red[q] + red[kNB + q]) + (red[2 * kNB + q] + red[3 * kNB + q]);
+        // top row c of the later panel columns (the e_c part of v_c)
+        d[q] = (q > jj && q < nbk) ? (acc[q] + Pt[jj + q * kNB]) * tau_c : 0.0;
+      }
+      // pass B: bottom rows 0..c of the later panel columns, and the squared
+      // norm of the next column's rows 0..c+1
+      nx = 0.0;
+      if (jj + 1 < nbk) {
+        for (int64_t i = tid; i <= c + 1; i += NT) {
+          const double u = (i <= c) ? Pb[i + jj * nr] : 0.0;
+#pragma unroll
+          for (int q = 0; q < kNB; ++q) {
+            if (q > jj && q < nbk) {
+              double a = Pb[i + q * nr];
+              if (i <= c) {
+                a -= d[q] * u;
+                Pb[i + q * nr] = a;
+              }
+              if (q == jj + 1) nx += a * a;
+            }
+          }
+        }
+      }
+      nx = warp_sum(nx);
+      if (lane == 0) red2[warp] = nx;
+      stage_bar();   // every thread has read red and Pt row jj
+      if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < kNB; ++q) Pd[q] = acc[q];
+        Pt[jj + jj * kNB] = beta;
+        tau_out[jj] = tau_c;
+        for (int p = 0; p < jj; ++p) {
+          double sacc = 0.0;
+          for (int q = p; q < jj; ++q) sacc += sT[p * kNB + q] * Pd[q];
+          sT[p * kNB + jj] = -tau_c * sacc;
+        }
+        sT[jj * kNB + jj] = tau_c;
+#pragma unroll
+        for (int q = 0; q < kNB; ++q)
+          if (q > jj && q < nbk) Pt[jj + q * kNB] -= d[q];
+      }
+      xx = red2[0] + red2[1] + red2[2] + red2[3];
+    }
+  }
+  __syncthreads();
+  for (int64_t idx = tid; idx < nr * nbk; idx += nthr) {
+    const int64_t i = idx % nr, q = idx / nr;
+    Rb[i + (k + q) * M] = Pb[i + q * nr];
+  }
+  for (int idx = tid; idx < nbk * nbk; idx += nthr) {
+    const int r = idx % nbk, q = idx / nbk;
+    Rt[(k + r) + (k + q) * M] = Pt[r + q * kNB];
+  }
+  __syncthreads();
+}
+
 // QR of [Rt; Rb] by panels of kNB columns: structured panel factorisation,
 // then the block reflector applied to the trailing columns on the FP64
 // tensor pipe (bottom rows 0..k+nbk-1 through u, top rows k..k+nbk-1 as the
@@ -274,7 +414,10 @@ static __device__ void tree_merge(double* Rt, double* Rb, double* tau, int64_t M
     const int nbk = (int)((M - k) < kNB ? (M - k) : kNB);
     for (int idx = tid; idx < kSmT; idx += nthr) sT[idx] = 0.0;
     __syncthreads();
-    merge_panel_factor(Rt, Rb, M, k, nbk, tau + k, sT, sred, sout);
+    if (merge_panel_staged(M))
+      merge_panel_factor_staged(Rt, Rb, M, k, nbk, tau + k, sT, sW);
+    else
+      merge_panel_factor(Rt, Rb, M, k, nbk, tau + k, sT, sred, sout);
     __syncthreads();
     if (k + nbk < M) {
       MergeV V{Rb, M, k, nbk};

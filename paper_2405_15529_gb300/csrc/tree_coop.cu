@@ -23,14 +23,18 @@ namespace pylom {
 // Factor panel [k, k+nbk) of merge j at tree step `step`; publish T to Tt
 // when trailing columns remain.
 static __device__ void coop_factor(const TsqrState& s, double* Tt, int64_t j, int64_t step, int64_t k, int nbk,
-                                   double* sT, double* sred, double* sout) {
+                                   double* sT, double* sred, double* sout, double* sP) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int64_t M = s.M;
   const int64_t left = j * 2 * step, right = left + step;
   for (int idx = tid; idx < kSmT; idx += nthr) sT[idx] = 0.0;
   __syncthreads();
-  merge_panel_factor(s.Rs + left * M * M, s.Rs + right * M * M, M, k, nbk, s.tau_tree + right * M + k, sT, sred,
-                     sout);
+  if (merge_panel_staged(M))
+    merge_panel_factor_staged(s.Rs + left * M * M, s.Rs + right * M * M, M, k, nbk, s.tau_tree + right * M + k, sT,
+                              sP);
+  else
+    merge_panel_factor(s.Rs + left * M * M, s.Rs + right * M * M, M, k, nbk, s.tau_tree + right * M + k, sT, sred,
+                       sout);
   __syncthreads();
   if (k + nbk < M) {
     for (int idx = tid; idx < kSmT; idx += nthr) Tt[idx] = sT[idx];
@@ -52,7 +56,7 @@ __global__ void __launch_bounds__(kLeafThreads, 2) tree_coop_kernel(TsqrState s)
     const int64_t m = (P - step + 2 * step - 1) / (2 * step);
     {
       const int nbk = (int)(M < kNB ? M : kNB);
-      for (int64_t j = blockIdx.x; j < m; j += G) coop_factor(s, s.Tt + j * kSmT, j, step, 0, nbk, sT, sred, sout);
+      for (int64_t j = blockIdx.x; j < m; j += G) coop_factor(s, s.Tt + j * kSmT, j, step, 0, nbk, sT, sred, sout, sW);
     }
     if (!grid_barrier(s.hdr, (unsigned)G)) return;
     // panel k is full width whenever trailing columns follow it
@@ -80,7 +84,7 @@ __global__ void __launch_bounds__(kLeafThreads, 2) tree_coop_kernel(TsqrState s)
         if (ch == 0) {
           // the next panel's columns are in this chunk (cw >= 2 kNB)
           const int nb2 = (int)(rem < kNB ? rem : kNB);
-          coop_factor(s, s.Tt + ((buf ^ 1) * half + j) * kSmT, j, step, c_begin, nb2, sT, sred, sout);
+          coop_factor(s, s.Tt + ((buf ^ 1) * half + j) * kSmT, j, step, c_begin, nb2, sT, sred, sout, sW);
         }
       }
       if (!grid_barrier(s.hdr, (unsigned)G)) return;

@@ -56,12 +56,12 @@ static_assert(2 * kWA + 2 * kWB <= kOpBytes, "W-stage operands must fit the oper
 constexpr int kOffW = kOpBytes;                    // W: 32 x 128 fp32 (16 KB)
 constexpr int kOffT = kOffW + kNB2 * kCH * 4;      // T: 32 x 32 fp64 (8 KB)
 // TMA ring of the factorisation's W stage: per 64-row step, the raw FP32
-// boxes of the C chunk (kTmaRows rows x 128 columns) and of the panel
-// (kTmaRows x 32), two stages.  A box starts at the row rounded down to a
-// multiple of 4 (16 bytes), so it holds 4 rows more than a step uses.
-constexpr int kTmaRows = kKC + 4;
-constexpr int kRawC = kTmaRows * kCH * 4;          // 34,816 B
-constexpr int kRawV = kTmaRows * kNB2 * 4;         // 8,704 B
+// boxes of the C chunk (64 rows x 128 columns) and of the panel (64 x 32),
+// two stages.  The steps start at the panel's first row rounded down to a
+// multiple of 4 (a 16-byte boundary), so every step's box is aligned.
+constexpr int kTmaRows = kKC;
+constexpr int kRawC = kTmaRows * kCH * 4;          // 32,768 B
+constexpr int kRawV = kTmaRows * kNB2 * 4;         // 8,192 B
 constexpr int kStageBytes = kRawC + kRawV;
 constexpr int kOffRaw = kOffT + kNB2 * kNB2 * 8;
 static_assert(kOffRaw % 128 == 0 && kRawC % 128 == 0, "TMA destinations must be 128-byte aligned");
@@ -568,10 +568,18 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
       // updates of C) are ordered before the tensor-memory-access reads
       asm volatile("fence.proxy.async;" ::: "memory");
       __syncthreads();
+      // steps cover working-copy rows xa + 64 kc .. xa + 64 kc + 63 from the
+      // panel's first row rounded down to a multiple of 4; rows of a step
+      // outside the panel's rows k .. h-1 (up to 3 above it, the ragged end
+      // below it, the other leaves' rows, rows past N read as zeros) meet a
+      // zero reflector entry, so the C tile is taken whole and only the
+      // reflector operand is masked
+      const int64_t xa = (tw.grow0 + k) & ~int64_t(3);
+      const int64_t ioff = xa - tw.grow0;          // leaf row of a step's first row, minus 64 kc
+      const int64_t nkt = (tw.grow0 + h - xa + kKC - 1) / kKC;
       auto issue = [&](int64_t kc) {   // thread 0
         const int st = (int)(kc & 1);
-        const int64_t g = tw.grow0 + k + kc * kKC;
-        const int32_t x0 = (int32_t)(g & ~int64_t(3));
+        const int32_t x0 = (int32_t)(xa + kc * kKC);
         unsigned char* dst = smem + kOffRaw + st * kStageBytes;
         fence_smem_async();
         mbar_arrive_expect_tx(&tw.fullbar[st], (uint32_t)kStageBytes);
@@ -580,10 +588,16 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
       };
       if (tid == 0) {
         issue(0);
-        if (nkc > 1) issue(1);
+        if (nkt > 1) issue(1);
       }
-      int64_t issued = nkc > 1 ? 2 : 1, consumed = 0;
-      for (int64_t kc = 0; kc < nkc && ok; ++kc) {
+      int64_t issued = nkt > 1 ? 2 : 1, consumed = 0;
+      // A-operand map: warp instruction u of warp w and lane 8 q + j move the
+      // 16 bytes (4 K elements) of operand row c = 8 cg + j, K group
+      // g = 8 gg + (j + s) % 8, with 32 u + 4 w + q = cg + 16 gg + 32 s: eight
+      // lanes read eight different 16-byte bank groups of the box and write
+      // eight different ones of the core-matrix tile
+      const int jl = lane & 7, ql = lane >> 3;
+      for (int64_t kc = 0; kc < nkt && ok; ++kc) {
         const int st = (int)(kc & 1);
         const bool got = mbar_wait(&tw.fullbar[st], (*tw.tphase >> st) & 1u);
         *tw.tphase ^= 1u << st;
@@ -592,28 +606,30 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
         if (!ok) break;
         const float* rc = (const float*)(smem + kOffRaw + st * kStageBytes);
         const float* rv = rc + kTmaRows * kCH;
-        const int off = (int)((tw.grow0 + k + kc * kKC) & 3);
-        const int64_t rbase = k + kc * kKC;        // leaf row of K element 0
-#pragma unroll 8
-        for (int u = 0; u < kCH / 4; ++u) {        // A: 16 row groups x 16 K groups
-          const int cmi = u * 8 + warp;
-          const int c = (cmi & 15) * 8 + lrow;
-          const int rk = (cmi >> 4) * 4 + lk;
-          const float x = (rbase + rk < h && c < wc) ? rc[c * kTmaRows + off + rk] : 0.f;
-          float hi, lo;
-          split_tf32(x, hi, lo);
-          const uint32_t o = cm_off(c, rk, kKC);
-          *(float*)(smem + kOffWA + o) = hi;
-          *(float*)(smem + kOffWAlo + o) = lo;
+#pragma unroll 2
+        for (int u = 0; u < 8; ++u) {
+          const int wq = u * 32 + warp * 4 + ql;
+          const int cg = wq & 15, gg = (wq >> 4) & 1, sh = wq >> 5;
+          const int c = cg * 8 + jl, g = gg * 8 + ((jl + sh) & 7);
+          const float4 x = *(const float4*)(rc + c * kTmaRows + 4 * g);
+          float4 hi, lo;
+          split_tf32(x.x, hi.x, lo.x);
+          split_tf32(x.y, hi.y, lo.y);
+          split_tf32(x.z, hi.z, lo.z);
+          split_tf32(x.w, hi.w, lo.w);
+          const uint32_t o = cm_off(c, 4 * g, kKC);
+          *(float4*)(smem + kOffWA + o) = hi;
+          *(float4*)(smem + kOffWAlo + o) = lo;
         }
+        const int64_t ibase = ioff + kc * kKC;    // leaf row of K element 0
 #pragma unroll
         for (int u = 0; u < kNB2 / 4; ++u) {       // B: 4 reflector groups x 16 K groups
           const int cmi = u * 8 + warp;
           const int pp = (cmi & 3) * 8 + lrow;
           const int rk = (cmi >> 2) * 4 + lk;
-          const int64_t i = rbase + rk, d = k + pp;
+          const int64_t i = ibase + rk, d = k + pp;
           float x = 0.f;
-          if (pp < nbk && i < h && i >= d) x = (i == d) ? 1.f : rv[pp * kTmaRows + off + rk];
+          if (pp < nbk && i < h && i >= d) x = (i == d) ? 1.f : rv[pp * kTmaRows + rk];
           float hi, lo;
           split_tf32(x, hi, lo);
           const uint32_t o = cm_off(pp, rk, kKC);
@@ -625,11 +641,11 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
         __syncthreads();     // the stage is read out: it may be refilled
         fence_after();
         if (tid == 0) {
-          if (kc + 2 < nkc) issue(kc + 2);
+          if (kc + 2 < nkt) issue(kc + 2);
           issue_3xtf32(tmem, tmem + kNB2, smem, kOffWA, kOffWAlo, kOffWB, kOffWBlo, kKC, idesc_tf32(128, kNB2));
           commit(mbar);
         }
-        if (kc + 2 < nkc) ++issued;
+        if (kc + 2 < nkt) ++issued;
         ok = mma_and_fold();
       }
       if (!ok) {
@@ -1010,8 +1026,9 @@ size_t mixed_extra_bytes(int64_t N, int64_t M, int64_t P) {
          align256(sizeof(float) * (size_t)(N / kCR + P + 1) * kHrSlot);
 }
 
-// Tensor map of the FP32 working copy (yf_ld(N) x M, column-major) with
-// boxes of kTmaRows rows x `cols` columns; out-of-range boxes read zeros.
+// Tensor map of the FP32 working copy (N x M, column-major, leading
+// dimension yf_ld(N)) with boxes of kTmaRows rows x `cols` columns;
+// out-of-range parts of a box read zeros.
 static cudaError_t encode_yf_map(CUtensorMap* map, float* Yf, int64_t N, int64_t M, int cols) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   static std::mutex mu;
@@ -1026,7 +1043,9 @@ static cudaError_t encode_yf_map(CUtensorMap* map, float* Yf, int64_t N, int64_t
       encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
   }
-  const cuuint64_t dims[2] = {(cuuint64_t)yf_ld(N), (cuuint64_t)M};
+  // rows past N (the padding of the leading dimension) are out of range:
+  // they read as zeros, never as uninitialised memory
+  const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)M};
   const cuuint64_t strides[1] = {(cuuint64_t)yf_ld(N) * sizeof(float)};
   const cuuint32_t box[2] = {(cuuint32_t)kTmaRows, (cuuint32_t)cols};
   const cuuint32_t estr[2] = {1, 1};

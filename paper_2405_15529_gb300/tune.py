@@ -1,10 +1,19 @@
-"""Autotuner of the batched complex SVD: the TSQR leaf height of each bin.
+"""Autotuner of the TSQR leaf heights.
 
-The leaf height trades the leaf QR's memory traffic (a taller leaf streams
-its trailing columns from HBM once per reflector) against the binary64 tree
-(P - 1 merges of (8/3) Nb^3 real flops each).  For every (Nb class, N class)
-the tuner times a small batch of seeded sample bins with each candidate
-height through the library's own batched launch and keeps the fastest.
+Batched complex SVD (SPOD bins and windows): the leaf height trades the leaf
+QR's memory traffic (a taller leaf streams its trailing columns from HBM once
+per reflector) against the binary64 tree (P - 1 merges of (8/3) Nb^3 real
+flops each).  For every (Nb class, N class) the tuner times a small batch of
+seeded sample bins with each candidate height through the library's own
+batched launch and keeps the fastest.
+
+POD (pylom_pod): the leaf count P trades the leaves' parallelism (one or two
+thread blocks per SM) and their panel latency against the tree's (P - 1)
+(2/3) M^3 binary64 flops.  For an (N, M, precision) the tuner times the POD
+of a seeded known-spectrum matrix of that shape at each candidate leaf count
+(whole multiples of the SM count, so every wave of leaves fills the GPU)
+and keeps the fastest leaf height.
+
 Results are cached in JSON, keyed by GPU name, precision and class; the cache
 file is a runtime artifact (PYLOM_TUNE_CACHE overrides its path).
 """
@@ -122,3 +131,72 @@ def leaf_rows_for(Ns, Nbs, prec: int, tune: bool = False):
     if dirty:
         _save(cache)
     return out
+
+
+# ---------------------------------------------------------------------------
+# POD leaf heights
+# ---------------------------------------------------------------------------
+
+def pod_candidates(N: int, M: int, prec: int, sms: int = 152):
+    """Leaf heights whose leaf counts are 1, 2, 3 or 4 thread blocks per SM
+    (the mixed path holds one block per SM at a time, so its counts stay
+    whole waves of one block per SM), keeping >= max(M, 1024) rows a leaf."""
+    per = (1, 2, 3, 4) if prec == pg.PREC_FP64 else (1, 2)
+    out = []
+    for k in per:
+        P = k * sms
+        b = N // P
+        if b >= max(M, 1024) and b not in out:
+            out.append(b)
+    return out
+
+
+def time_pod(N: int, M: int, prec: int, leaf_rows: int, reps: int = 3, seed: int = 0) -> float:
+    """Median seconds of pylom_pod on a seeded N x M known-spectrum matrix."""
+    import torch
+    import synth
+    dt = torch.float64 if prec == pg.PREC_FP64 else torch.float32
+    XT, w, _ = synth.known_spectrum_torch(N, M, device="cuda", dtype=dt, seeds=(2 + seed, 3, 4))
+    X = XT.t()
+    ws = torch.empty(pg.pod_workspace_size(N, M, leaf_rows, M, pg.F64 if dt == torch.float64 else pg.F32, prec),
+                     dtype=torch.uint8, device="cuda")
+    res = pg.pod(X, w=w, remove_mean=False, energy=0.99, leaf_rows=leaf_rows, prec=prec, workspace=ws)
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pg.pod(X, w=w, remove_mean=False, energy=0.99, leaf_rows=leaf_rows, prec=prec, workspace=ws, check=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) * 1e-3)
+    st, _, _ = pg.workspace_status(ws)
+    if st != pg.OK:
+        raise pg.PylomError(st, "autotuner POD run")
+    del X, XT, ws, res
+    torch.cuda.empty_cache()
+    ts.sort()
+    return ts[len(ts) // 2]
+
+
+def tune_pod(N: int, M: int, prec: int, sms: int = None):
+    """Times every candidate leaf height; returns (fastest height, {height: s})."""
+    import torch
+    if sms is None:
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+    times = {b: time_pod(N, M, prec, b) for b in pod_candidates(N, M, prec, sms)}
+    if not times:
+        return 0, times      # too few rows for a full wave of leaves: the automatic choice
+    best = min(times, key=lambda b: (times[b], b))
+    return best, times
+
+
+def pod_leaf_rows_for(N: int, M: int, prec: int, tune: bool = False) -> int:
+    """The cached leaf height for this (N, M, precision) -- tuned first when
+    `tune` and not cached -- or 0 (the library's automatic choice)."""
+    key = f"{gpu_name()}|pod|prec{prec}|N{N}|M{M}"
+    cache = _load()
+    if key not in cache and tune:
+        cache[key] = tune_pod(N, M, prec)[0]
+        _save(cache)
+    return int(cache.get(key, 0))

@@ -2,8 +2,8 @@
 streamed through the device in chunks of whole leaves): it runs the same
 kernels on the same leaves as the in-core call, so its results must equal
 those of pylom_pod with the same leaf partition bit for bit -- for the
-last-arriver tree (M < 384), whose merges span chunk launches, and for the
-cooperative tree (M >= 384), launched once after the last chunk -- and the
+last-arriver tree (M < 384 and fewer than 64 leaves), whose merges span chunk launches, and for the
+cooperative tree (M >= 384 or 64 leaves), launched once after the last chunk -- and the
 FP64 oracle's within the parity tolerances."""
 import numpy as np
 import pytest

@@ -80,3 +80,32 @@ def test_tuned_height_is_fastest_and_is_run(tmp_path, monkeypatch):
         assert b.info(f, 1) == max(1, N // heights[f], -(-N // hmax))
     b.run()
     assert b.status() == pg.OK
+
+
+def test_pod_candidates_are_whole_waves():
+    # 4,194,304 x 256: 152, 304, 456, 608 leaves (FP64), 152 and 304 (mixed)
+    c = tune.pod_candidates(1 << 22, 256, pg.PREC_FP64, sms=152)
+    assert c == [(1 << 22) // (k * 152) for k in (1, 2, 3, 4)]
+    assert tune.pod_candidates(1 << 22, 256, pg.PREC_MIXED_3XTF32, sms=152) == c[:2]
+    # leaves never below max(M, 1024) rows
+    assert all(b >= 1808 for b in tune.pod_candidates(10_000_000, 1808, pg.PREC_FP64, sms=152))
+    assert tune.pod_candidates(100_000, 256, pg.PREC_FP64, sms=152) == []
+
+
+def test_pod_cache_round_trip(tmp_path, monkeypatch):
+    monkeypatch.setattr(tune, "CACHE", str(tmp_path / "c.json"))
+    monkeypatch.setattr(tune, "gpu_name", lambda: "cpu")
+    assert tune.pod_leaf_rows_for(1 << 22, 256, pg.PREC_FP64, tune=False) == 0
+    tune._save({"cpu|pod|prec0|N4194304|M256": 13797})
+    assert tune.pod_leaf_rows_for(1 << 22, 256, pg.PREC_FP64, tune=False) == 13797
+
+
+@pytest.mark.gpu
+def test_pod_tuner_picks_fastest_and_result_holds(tmp_path, monkeypatch):
+    torch = pytest.importorskip("torch")
+    monkeypatch.setattr(tune, "CACHE", str(tmp_path / "cache.json"))
+    N, M = 1 << 19, 64
+    best, times = tune.tune_pod(N, M, pg.PREC_FP64)
+    assert times and times[best] == min(times.values())
+    assert tune.pod_leaf_rows_for(N, M, pg.PREC_FP64, tune=True) in times
+    assert pg.leaf_count(N, M, best) == N // best
