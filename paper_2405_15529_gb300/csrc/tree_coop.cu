@@ -9,9 +9,9 @@
 // merges advance panel by panel (kNB columns): the trailing columns of each
 // merge are cut into chunks, one block per (merge, chunk) applies the
 // panel's block reflector, and the block holding a merge's first chunk --
-// which contains the next panel's columns -- then factors that panel and
-// publishes its T factor (double-buffered), so a single bounded grid barrier
-// separates consecutive panels.  The pairing (left child's R on top), the
+// exactly the next panel's columns, so that block's update is short -- then
+// factors that panel and publishes its T factor (double-buffered), so a
+// single bounded grid barrier separates consecutive panels.  The pairing (left child's R on top), the
 // merged R in the left slot and the node reflectors in the right slot are
 // those of the last-arriver tree, so the top-down pass and the adjoint read
 // them unchanged.
@@ -59,14 +59,20 @@ __global__ void __launch_bounds__(kLeafThreads, 2) tree_coop_kernel(TsqrState s)
       for (int64_t j = blockIdx.x; j < m; j += G) coop_factor(s, s.Tt + j * kSmT, j, step, 0, nbk, sT, sred, sout, sW);
     }
     if (!grid_barrier(s.hdr, (unsigned)G)) return;
-    // panel k is full width whenever trailing columns follow it
+    // panel k is full width whenever trailing columns follow it.  Chunk 0
+    // of a merge is exactly the next panel's columns: its block updates them
+    // and factors that panel at once (the critical path of a grid step),
+    // while the other blocks update the remaining columns in chunks.
     for (int64_t k = 0; k + kNB < M; k += kNB) {
       const int64_t c_begin = k + kNB, rem = M - c_begin;
+      const int64_t w0 = rem < kNB ? rem : kNB;       // chunk 0: the next panel
+      const int64_t rem2 = rem - w0;                   // the rest
       const int64_t per_merge = (G + m - 1) / m;
-      int64_t cw = (rem + per_merge - 1) / per_merge;
+      const int64_t helpers = per_merge > 1 ? per_merge - 1 : 1;
+      int64_t cw = (rem2 + helpers - 1) / helpers;
       cw = (cw + 7) & ~int64_t(7);
       cw = cw < 2 * kNB ? 2 * kNB : (cw > kCW ? kCW : cw);
-      const int64_t nch = (rem + cw - 1) / cw;
+      const int64_t nch = 1 + (rem2 + cw - 1) / cw;
       const int64_t buf = (k / kNB) & 1;
       for (int64_t item = blockIdx.x; item < m * nch; item += G) {
         const int64_t j = item / nch, ch = item - j * nch;
@@ -76,16 +82,14 @@ __global__ void __launch_bounds__(kLeafThreads, 2) tree_coop_kernel(TsqrState s)
         const double* Tg = s.Tt + (buf * half + j) * kSmT;
         for (int idx = tid; idx < kSmT; idx += nthr) sT[idx] = ldcg(Tg + idx);
         __syncthreads();
-        const int64_t c0 = c_begin + ch * cw;
-        const int wc = (int)((M - c0) < cw ? (M - c0) : cw);
+        const int64_t c0 = (ch == 0) ? c_begin : c_begin + w0 + (ch - 1) * cw;
+        const int64_t cwi = (ch == 0) ? w0 : cw;
+        const int wc = (int)((M - c0) < cwi ? (M - c0) : cwi);
         MergeV V{Rb, M, k, kNB};
         block_reflector<true, true>(V, kNB, 0, k + kNB, Rb + c0 * M, M, wc, Rt + k + c0 * M, M, sT, sW, sWp);
         __syncthreads();
-        if (ch == 0) {
-          // the next panel's columns are in this chunk (cw >= 2 kNB)
-          const int nb2 = (int)(rem < kNB ? rem : kNB);
-          coop_factor(s, s.Tt + ((buf ^ 1) * half + j) * kSmT, j, step, c_begin, nb2, sT, sred, sout, sW);
-        }
+        if (ch == 0)
+          coop_factor(s, s.Tt + ((buf ^ 1) * half + j) * kSmT, j, step, c_begin, (int)w0, sT, sred, sout, sW);
       }
       if (!grid_barrier(s.hdr, (unsigned)G)) return;
     }

@@ -622,19 +622,31 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
           *(float4*)(smem + kOffWAlo + o) = lo;
         }
         const int64_t ibase = ioff + kc * kKC;    // leaf row of K element 0
+        // B operand (32 reflectors x 64 K), the same map on 4 row groups:
+        // entry (i, p) of the panel's reflector matrix -- zero above the
+        // diagonal and past the leaf, one on it
 #pragma unroll
-        for (int u = 0; u < kNB2 / 4; ++u) {       // B: 4 reflector groups x 16 K groups
-          const int cmi = u * 8 + warp;
-          const int pp = (cmi & 3) * 8 + lrow;
-          const int rk = (cmi >> 2) * 4 + lk;
-          const int64_t i = ibase + rk, d = k + pp;
-          float x = 0.f;
-          if (pp < nbk && i < h && i >= d) x = (i == d) ? 1.f : rv[pp * kTmaRows + rk];
-          float hi, lo;
-          split_tf32(x, hi, lo);
-          const uint32_t o = cm_off(pp, rk, kKC);
-          *(float*)(smem + kOffWB + o) = hi;
-          *(float*)(smem + kOffWBlo + o) = lo;
+        for (int u = 0; u < 2; ++u) {
+          const int wq = u * 32 + warp * 4 + ql;
+          const int cg = wq & 3, gg = (wq >> 2) & 1, sh = wq >> 3;
+          const int pp = cg * 8 + jl, g = gg * 8 + ((jl + sh) & 7);
+          const float4 raw = *(const float4*)(rv + pp * kTmaRows + 4 * g);
+          const int64_t d = k + pp;
+          const int64_t i0 = ibase + 4 * g;
+          float x[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int64_t i = i0 + e;
+            x[e] = (pp < nbk && i < h && i >= d) ? ((i == d) ? 1.f : x[e]) : 0.f;
+          }
+          float4 hi, lo;
+          split_tf32(x[0], hi.x, lo.x);
+          split_tf32(x[1], hi.y, lo.y);
+          split_tf32(x[2], hi.z, lo.z);
+          split_tf32(x[3], hi.w, lo.w);
+          const uint32_t o = cm_off(pp, 4 * g, kKC);
+          *(float4*)(smem + kOffWB + o) = hi;
+          *(float4*)(smem + kOffWBlo + o) = lo;
         }
         fence_smem_async();
         fence_before();
