@@ -27,6 +27,13 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "POD GB/s of X processed"
+# DRAM bytes (read + write) of one leaf_qr_kernel launch on the 4,194,304 x 256
+# workload (304 leaves), from a one-pass ncu capture of that launch inside
+# this benchmark (dram__bytes_read.sum + dram__bytes_write.sum); see the
+# profile summary of the FP64 path.
+LEAF_FP64_TRAFFIC_BYTES = 420.31e9 + 155.16e9
+LEAF_FP64_TRAFFIC_SOURCE = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:leaf_qr_kernel, "
+                            "full-size launch (1 pass), profiles/pod_fp64_known_spectrum_4194304x256.md")
 N_FULL, M_FULL, ENERGY = 1 << 22, 256, 0.99
 WORKLOAD = "known_spectrum_4194304x256_f64_weighted_energy0.99"
 
@@ -359,7 +366,7 @@ def bench_mixed(args, dev):
     torch.cuda.synchronize()
     ms64 = t0.elapsed_time(t1)
     S64 = ref.S.cpu().numpy()
-    leaf_ms = phases["leaf_qr_tree"] / max(n, 1)
+    leaf_ms = phases["leaf_qr"] / max(n, 1)
     out = {"workload": f"known_spectrum_{N}x{M}_f32_weighted_energy0.99", "status": st, "r": r,
            "leaf_rows": leaf, "leaves": pg.leaf_count(N, M, leaf) if leaf else min(152, pg.leaf_count(N, M, 0)),
            "ms_per_step": ms, "value": N * M * 4 / (ms * 1e-3) / 1e9, "unit": "GB/s of X (float32)",
@@ -367,7 +374,7 @@ def bench_mixed(args, dev):
            "fp64_path_ms_same_x": ms64, "speedup_vs_fp64_path": ms64 / ms,
            "sigma_max_abs_diff_vs_fp64_path_over_smax": float(np.max(np.abs(S_mix - S64)) / S64[0]),
            "sigma_max_abs_err_vs_closed_form_over_smax": float(np.max(np.abs(S_mix - s)) / s[0]),
-           "leaf_kernel": {"kernel": "leaf_qr_mixed_kernel (FP32 panels + 3xTF32 tcgen05 trailing updates + FP64 tree)",
+           "leaf_kernel": {"kernel": "leaf_qr_mixed_kernel (FP32 panels + 3xTF32 tcgen05 trailing updates)",
                            "ms_per_launch": leaf_ms,
                            "useful_tflops": 2.0 * N * M * M / (leaf_ms * 1e-3) / 1e12}}
     del X, XT, w, ws, U, S, VT, r_dev, ref
@@ -667,24 +674,27 @@ def bench_waves_1808(args, dev):
     hbm = peaks.get("hbm_gbs", 6800.0)
     tf32_3x = peaks.get("bf16_tflops", 1900.0) * 0.5 / 3.0     # nominal tf32/bf16 = 1/2; three MMAs per product
     t_roof = max(bytes_x / (hbm * 1e9), 2.0 * N * M * M / (tf32_3x * 1e12))
-    leaf_ms = mix["phases_ms"]["leaf_qr_tree"]
+    leaf_ms = mix["phases_ms"]["leaf_qr"]
+    tree_ms = mix["phases_ms"]["tree"]
     # dominant kernel of the mixed step: the leaves (FP32 panels + 3xTF32
-    # trailing updates, 2NM^2 - (2/3)PM^3 flops as three TF32 products) and
-    # the binary64 tree that follows them in the same phase
+    # trailing updates, 2NM^2 - (2/3)PM^3 flops as three TF32 products); the
+    # binary64 cooperative tree that follows is reported beside it
     P = pg.leaf_count(N, M, 0)
     P = min(P, 152) if P > 152 else P
     leaf_flops = 2.0 * N * M * M - (2.0 / 3.0) * P * M ** 3
     tree_flops = (P - 1) * (2.0 / 3.0) * M ** 3
     fp64_peak = probe_peak("mma")
-    t_kernel_roof = leaf_flops / (tf32_3x * 1e12) + tree_flops / (fp64_peak * 1e12)
+    leaf_bytes = N * M * 4 + N * M * 4      # read X (FP32), write the FP32 reflectors
+    t_leaf_roof = max(leaf_flops / (tf32_3x * 1e12), leaf_bytes / (hbm * 1e9))
     roofline = {"bound": "tensor", "achieved": leaf_flops / (leaf_ms * 1e-3) / 1e12, "peak": tf32_3x,
-                "unit": "TFLOP/s", "frac": t_kernel_roof / (leaf_ms * 1e-3), "traffic": None,
-                "kernel": "leaf_qr_mixed_kernel + tree_coop_kernel (phase leaf_qr_tree)",
-                "peak_source": "3xTF32 = measured bf16 burst x nominal tf32/bf16 (1/2) / 3; the tree's "
-                               "binary64 flops at the measured FP64 mma probe rate",
-                "algorithmic_flops_per_launch": {"leaf_3xtf32": leaf_flops, "tree_fp64": tree_flops},
-                "frac_formula": "(leaf_flops/tf32_3x_peak + tree_flops/fp64_peak) / phase time",
-                "ms_per_launch": leaf_ms, "leaves": P}
+                "unit": "TFLOP/s", "frac": t_leaf_roof / (leaf_ms * 1e-3), "traffic": None,
+                "kernel": "leaf_qr_mixed_kernel",
+                "peak_source": "3xTF32 = measured bf16 burst x nominal tf32/bf16 (1/2) / 3",
+                "algorithmic_flops_per_launch": leaf_flops, "algorithmic_bytes_per_launch": leaf_bytes,
+                "ms_per_launch": leaf_ms, "leaves": P,
+                "tree": {"kernel": "tree_coop_kernel (binary64)", "ms_per_launch": tree_ms,
+                         "algorithmic_flops_per_launch": tree_flops, "peak_fp64_tflops": fp64_peak,
+                         "frac": tree_flops / (fp64_peak * 1e12) / (tree_ms * 1e-3) if tree_ms > 0 else None}}
     cpu = {"skipped": "the oracle's unblocked QR and cyclic Jacobi at 1808 columns take minutes even on a "
                       "row sample; run bench.py --c3-cpu for the extrapolated figure"}
     if args.c3_cpu:
@@ -706,7 +716,7 @@ def bench_waves_1808(args, dev):
                              "formula": "max(bytes_X/HBM_peak, 2NM^2/(tf32_peak/3)) / step time",
                              "tf32_peak_tflops": peaks.get("bf16_tflops", 1900.0) * 0.5,
                              "hbm_peak_gbs": hbm},
-            "leaf_kernel": {"kernel": "leaf_qr_mixed_kernel + tree_coop_kernel", "ms_per_step": leaf_ms,
+            "leaf_kernel": {"kernel": "leaf_qr_mixed_kernel", "ms_per_step": leaf_ms,
                             "useful_tflops": 2.0 * N * M * M / (leaf_ms * 1e-3) / 1e12}}
 
 
@@ -866,9 +876,15 @@ def run_ours(args, rank, world, local_rank):
     bytes_x = N * M * 8
     value = job_gbs(bytes_x, ms, world)
 
-    # dominant kernel: leaf QR + tree (one launch per step)
-    leaf_ms = phases["leaf_qr_tree"] / max(ncalls, 1)
-    flops_leaf = 2.0 * N * M * M - (2.0 / 3.0) * P * M ** 3 + (P - 1) * (2.0 / 3.0) * M ** 3
+    # dominant kernel: the leaf QR kernel (one launch per step).  When the
+    # tree runs as its own cooperative kernel (from 64 leaves) the leaf
+    # kernel's work is the leaves' 2NM^2 - (2/3)PM^3; when the leaves merge
+    # as they finish, the tree's (P - 1)(2/3)M^3 is in the same launch.
+    leaf_ms = phases["leaf_qr"] / max(ncalls, 1)
+    tree_ms = phases["tree"] / max(ncalls, 1)
+    coop_tree = tree_ms > 0.0
+    flops_tree = (P - 1) * (2.0 / 3.0) * M ** 3
+    flops_leaf = 2.0 * N * M * M - (2.0 / 3.0) * P * M ** 3 + (0.0 if coop_tree else flops_tree)
     achieved = flops_leaf / (leaf_ms * 1e-3) / 1e12
     hbm_peak = None
     try:
@@ -991,12 +1007,19 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "inputs (8.6 GB per rank) larger than L2 (129 MB); no flush",
                        "parallelism": f"independent problems x{world}"},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_mma, "unit": "TFLOP/s",
-                         "frac": achieved / peak_mma, "traffic": None,
-                         "kernel": "leaf_qr_kernel (leaf Householder QR + tree merges)",
+                         "frac": achieved / peak_mma, "traffic": LEAF_FP64_TRAFFIC_BYTES if (
+                             N == N_FULL and M == M_FULL and P == 304) else None,
+                         "traffic_source": LEAF_FP64_TRAFFIC_SOURCE,
+                         "algorithmic_bytes_per_launch": (8 + 8) * N * M,
+                         "kernel": "leaf_qr_kernel (leaf Householder QR%s)" % (
+                             "; the tree is its own kernel" if coop_tree else " + tree merges"),
                          "peak_source": "measured live: FP64 mma.sync.m8n8k4 throughput probe with "
                                         "independent chains (bench_probe.cu; MEASURED_PEAKS.json has no "
                                         "FP64 figure); cross-checked by the FP64 4096^3 product",
-                         "algorithmic_flops_per_launch": flops_leaf, "ms_per_launch": leaf_ms},
+                         "algorithmic_flops_per_launch": flops_leaf, "ms_per_launch": leaf_ms,
+                         "tree": {"kernel": "tree_coop_kernel", "ms_per_launch": tree_ms,
+                                  "algorithmic_flops_per_launch": flops_tree,
+                                  "achieved_tflops": flops_tree / (tree_ms * 1e-3) / 1e12 if coop_tree else None}},
             "pct_roofline_pod": {"value": pct_roof,
                                  "formula": "max(bytes_X/HBM_peak, 2NM^2/FP64_mma_peak) / step time",
                                  "hbm_peak_gbs": hbm_peak, "fp64_mma_tflops": peak_mma,

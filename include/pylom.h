@@ -504,15 +504,17 @@ pylom_status pylom_wait_selftest(int kind, int blocks, double limit_ms, unsigned
  * Phase profiler (measurement support; no counterpart in the paper).
  * Between begin and end, each of the next max_calls pylom_pod calls records
  * CUDA events on its own stream at the boundaries of its phases:
- *   0 leaf Householder QR + tree reduction (one kernel),
- *   1 small SVD (Jacobi + sort/sign/truncate),
- *   2 top-down pass of the tree,
- *   3 leaf modes product U = Q [B; 0].
+ *   0 leaf Householder QR (the leaf kernel; it includes the tree merges
+ *     when the leaves merge as they finish),
+ *   1 cooperative tree reduction (zero when the leaves merged),
+ *   2 small SVD (Jacobi + sort/sign/truncate),
+ *   3 top-down pass of the tree,
+ *   4 leaf modes product U = Q [B; 0].
  * pylom_profile_end synchronises on the recorded events and writes to HOST
  * memory the summed milliseconds per phase (phase_ms[PYLOM_PROFILE_PHASES])
  * and the number of calls recorded.  Host-global state: not thread-safe.
  * ------------------------------------------------------------------------ */
-#define PYLOM_PROFILE_PHASES 4
+#define PYLOM_PROFILE_PHASES 5
 pylom_status pylom_profile_begin(int max_calls);
 pylom_status pylom_profile_end(double* phase_ms, int* calls);
 

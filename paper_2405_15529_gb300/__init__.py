@@ -48,7 +48,7 @@ EXPORTS = (
     "pylom_pod_shard_workspace_size", "pylom_pod_shard_factor", "pylom_pod_rstack_workspace_size",
     "pylom_pod_rstack", "pylom_pod_shard_modes",
 )
-PROFILE_PHASES = ("leaf_qr_tree", "svd_small", "down_pass", "modes")
+PROFILE_PHASES = ("leaf_qr", "tree", "svd_small", "down_pass", "modes")
 
 
 class PylomError(RuntimeError):
@@ -218,7 +218,9 @@ def profile_end():
     arr = (ctypes.c_double * len(PROFILE_PHASES))()
     n = _int(0)
     _raise(load_library().pylom_profile_end(arr, ctypes.byref(n)), "pylom_profile_end")
-    return dict(zip(PROFILE_PHASES, list(arr))), int(n.value)
+    out = dict(zip(PROFILE_PHASES, list(arr)))
+    out["leaf_qr_tree"] = out["leaf_qr"] + out["tree"]     # the leaves and the whole reduction
+    return out, int(n.value)
 
 
 def wait_selftest(kind: str = "grid", blocks: int = 16, limit_ms: float = 2.0, stream=None):

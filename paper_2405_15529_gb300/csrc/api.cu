@@ -187,22 +187,22 @@ extern "C" pylom_status pylom_pod(const void* X, int64_t N, int64_t M, int64_t l
   e = cudaMemsetAsync(ts.arrive, 0, sizeof(unsigned) * (size_t)P, st);
   if (e != cudaSuccess) return cuda_fail(e, "pylom_pod: counter clear");
   if (prof && (e = cudaEventRecord(g_prof.at(call, 0), st)) != cudaSuccess) return cuda_fail(e, "profile");
-  e = mixed ? launch_tsqr_mixed(ts, extra, X, ldx, xtype, w, remove_mean, mean, st)
-            : launch_tsqr_fp64(ts, X, ldx, xtype, w, remove_mean, mean, st);
+  e = mixed ? launch_tsqr_mixed(ts, extra, X, ldx, xtype, w, remove_mean, mean, st, prof ? g_prof.at(call, 1) : nullptr)
+            : launch_tsqr_fp64(ts, X, ldx, xtype, w, remove_mean, mean, st, prof ? g_prof.at(call, 1) : nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "pylom_pod: leaf QR / tree");
-  if (prof && (e = cudaEventRecord(g_prof.at(call, 1), st)) != cudaSuccess) return cuda_fail(e, "profile");
+  if (prof && (e = cudaEventRecord(g_prof.at(call, 2), st)) != cudaSuccess) return cuda_fail(e, "profile");
   e = launch_svd_fp64(ss, ts.Rs, M, UR, M, S, VT, ldvt, 60, energy, r_max, st);
   if (e != cudaSuccess) return cuda_fail(e, "pylom_pod: small SVD");
-  if (prof && (e = cudaEventRecord(g_prof.at(call, 2), st)) != cudaSuccess) return cuda_fail(e, "profile");
+  if (prof && (e = cudaEventRecord(g_prof.at(call, 3), st)) != cudaSuccess) return cuda_fail(e, "profile");
   if (mixed)
     e = launch_modes_mixed(ts, extra, UR, M, -1, w, mode_kind == PYLOM_MODES_PHYSICAL, (float*)U, ldu, r_out, st,
-                           prof ? g_prof.at(call, 3) : nullptr);
+                           prof ? g_prof.at(call, 4) : nullptr);
   else
     e = launch_modes_fp64(ts, UR, M, -1, w, mode_kind == PYLOM_MODES_PHYSICAL, (double*)U, ldu, r_out, st,
-                          prof ? g_prof.at(call, 3) : nullptr);
+                          prof ? g_prof.at(call, 4) : nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "pylom_pod: modes");
   if (prof) {
-    if ((e = cudaEventRecord(g_prof.at(call, 4), st)) != cudaSuccess) return cuda_fail(e, "profile");
+    if ((e = cudaEventRecord(g_prof.at(call, 5), st)) != cudaSuccess) return cuda_fail(e, "profile");
     ++g_prof.n;
   }
   return PYLOM_OK;

@@ -69,8 +69,10 @@ void svd_state_carve(SvdState& s, char* base, int64_t M);
 
 // Leaf QR of every row block (with fused mean/weight prologue) and the
 // last-arriver tree reduction; the root R ends in Rs[0].
+// `mid` (nullable) is recorded between the leaf kernel and the cooperative tree.
 cudaError_t launch_tsqr_fp64(const TsqrState& s, const void* X, int64_t ldx, int xtype,
-                             const double* w, int remove_mean, double* mean, cudaStream_t st);
+                             const double* w, int remove_mean, double* mean, cudaStream_t st,
+                             cudaEvent_t mid = nullptr);
 
 // The tree reduction as one cooperative launch over all blocks (for large
 // M); runs after the leaf kernel when s.climb == 0.
@@ -132,7 +134,8 @@ cudaError_t launch_down_pass_fp64(const TsqrState& s, const double* Ur, int64_t 
 // panel factors in an extra region; 3xTF32 block reflectors on tcgen05.
 size_t mixed_extra_bytes(int64_t N, int64_t M, int64_t P);
 cudaError_t launch_tsqr_mixed(const TsqrState& s, char* extra, const void* X, int64_t ldx, int xtype,
-                              const double* w, int remove_mean, double* mean, cudaStream_t st);
+                              const double* w, int remove_mean, double* mean, cudaStream_t st,
+                              cudaEvent_t mid = nullptr);
 cudaError_t launch_modes_mixed(const TsqrState& s, char* extra, const double* Ur, int64_t ldur, int64_t r_fixed,
                                const double* w, int physical, float* U, int64_t ldu, int64_t* r_out,
                                cudaStream_t st, cudaEvent_t mid);

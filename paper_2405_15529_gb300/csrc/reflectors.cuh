@@ -219,15 +219,17 @@ static __device__ void merge_panel_factor(double* Rt, double* Rb, int64_t M, int
       for (int q = 0; q < kNB; ++q)
         if (q < nbk && q != jj) acc[q] += u * ldcg(Rb + i + (k + q) * M);
     }
-    block_sum<kNB>(acc, sred, sout);
+    static_assert(kNB == 16, "the reduce-scatter sums 16 panel columns");
+    block_sum16(acc, sred, sout);
+    // column jj of T, one row per thread (rows 0..jj-1)
+    if (tid < jj) {
+      double s = 0.0;
+      for (int q = tid; q < jj; ++q) s += sT[tid * kNB + q] * sout[q];
+      sT[tid * kNB + jj] = -tau_c * s;
+    }
     if (tid == 0) {
       Rt[c + c * M] = beta;
       tau_out[jj] = tau_c;
-      for (int p = 0; p < jj; ++p) {
-        double s = 0.0;
-        for (int q = p; q < jj; ++q) s += sT[p * kNB + q] * sout[q];
-        sT[p * kNB + jj] = -tau_c * s;
-      }
       sT[jj * kNB + jj] = tau_c;
     }
     if (tid > jj && tid < nbk) {
@@ -272,7 +274,7 @@ static __device__ void merge_panel_factor(double* Rt, double* Rb, int64_t M, int
 // back.  The arithmetic is the column sweep above, term for term; only the
 // order of the partial sums differs.  The other warps of the block wait.
 // sP: (k + nbk) * kNB + kNB * kNB + kMergeStageExtra doubles of shared memory.
-constexpr int kMergeStageExtra = kNB + 4 * kNB + 4 + 4;
+constexpr int kMergeStageExtra = 4 * kNB + 4 + 4 + 2 * kNB;
 constexpr int kMergeStageThreads = 128;
 constexpr int64_t kMergeStageDoubles = 2 * kSmW;   // the sW / sWp buffers, free while a panel is factored
 __host__ __device__ constexpr bool merge_panel_staged(int64_t M) {
@@ -288,10 +290,11 @@ static __device__ void merge_panel_factor_staged(double* Rt, double* Rb, int64_t
   const int64_t nr = k + nbk;
   double* Pb = sP;               // Pb[i + q nr] = Rb[i, k + q], rows 0 .. nr-1
   double* Pt = sP + nr * kNB;    // Pt[r + q kNB] = Rt[k + r, k + q]
-  double* Pd = Pt + kNB * kNB;   // the column step's dot products, for the T recurrence
-  double* red = Pd + kNB;        // per-warp partial dot products (4 x kNB)
+  double* red = Pt + kNB * kNB;  // per-warp partial dot products (4 x kNB)
   double* red2 = red + 4 * kNB;  // per-warp partial norms
   double* sc = red2 + 4;         // tau, beta, scale of the current column
+  double* sdot = sc + 4;         // the column step's dot products (kNB)
+  double* sdv = sdot + kNB;      // the multiples of v_c subtracted from the later columns (kNB)
   for (int64_t idx = tid; idx < nr * nbk; idx += nthr) {
     const int64_t i = idx % nr, q = idx / nr;
     Pb[i + q * nr] = ldcg(Rb + i + (k + q) * M);
@@ -338,19 +341,24 @@ static __device__ void merge_panel_factor_staged(double* Rt, double* Rb, int64_t
         for (int q = 0; q < kNB; ++q)
           if (q < nbk && q != jj) acc[q] += u * Pb[i + q * nr];
       }
-#pragma unroll
-      for (int q = 0; q < kNB; ++q) {
-        const double v = warp_sum(acc[q]);
-        if (lane == 0) red[warp * kNB + q] = v;
+      {
+        const double t = warp_reduce_scatter16(acc);
+        if ((lane & 1) == 0) red[warp * kNB + ((lane >> 1) & 15)] = t;
+      }
+      stage_bar();
+      // thread q totals column q's dot product and, for the later panel
+      // columns, the multiple d_q of v_c to subtract (the e_c part of v_c
+      // meets the top row c)
+      if (tid < kNB) {
+        const int q = tid;
+        const double tq = (red[q] + red[kNB + q]) + (red[2 * kNB + q] + red[3 * kNB + q]);
+        sdot[q] = tq;
+        sdv[q] = (q > jj && q < nbk) ? (tq + Pt[jj + q * kNB]) * tau_c : 0.0;
       }
       stage_bar();
       double d[kNB];
 #pragma unroll
-      for (int q = 0; q < kNB; ++q) {
-        acc[q] = (red[q] + red[kNB + q]) + (red[2 * kNB + q] + red[3 * kNB + q]);
-        // top row c of the later panel columns (the e_c part of v_c)
-        d[q] = (q > jj && q < nbk) ? (acc[q] + Pt[jj + q * kNB]) * tau_c : 0.0;
-      }
+      for (int q = 0; q < kNB; ++q) d[q] = sdv[q];
       // pass B: bottom rows 0..c of the later panel columns, and the squared
       // norm of the next column's rows 0..c+1
       nx = 0.0;
@@ -373,16 +381,15 @@ static __device__ void merge_panel_factor_staged(double* Rt, double* Rb, int64_t
       nx = warp_sum(nx);
       if (lane == 0) red2[warp] = nx;
       stage_bar();   // every thread has read red and Pt row jj
+      // column jj of T, one row per thread (rows 0..jj-1)
+      if (tid < jj) {
+        double sacc = 0.0;
+        for (int q = tid; q < jj; ++q) sacc += sT[tid * kNB + q] * sdot[q];
+        sT[tid * kNB + jj] = -tau_c * sacc;
+      }
       if (tid == 0) {
-#pragma unroll
-        for (int q = 0; q < kNB; ++q) Pd[q] = acc[q];
         Pt[jj + jj * kNB] = beta;
         tau_out[jj] = tau_c;
-        for (int p = 0; p < jj; ++p) {
-          double sacc = 0.0;
-          for (int q = p; q < jj; ++q) sacc += sT[p * kNB + q] * Pd[q];
-          sT[p * kNB + jj] = -tau_c * sacc;
-        }
         sT[jj * kNB + jj] = tau_c;
 #pragma unroll
         for (int q = 0; q < kNB; ++q)

@@ -65,7 +65,7 @@ __device__ void panel_factor(double* A, int64_t lda, int64_t k, int nbk, int64_t
       for (int c = 0; c < kNB; ++c)
         if (c < nbk && c != jj) acc[c] += v * A[i + (k + c) * lda];
     }
-    block_sum<kNB>(acc, sred, sout);
+    block_sum16(acc, sred, sout);
     if (tid == 0) {
       A[j + j * lda] = beta;
       tau_out[jj] = tau_j;
@@ -346,13 +346,14 @@ void tsqr_state_carve(TsqrState& s, char* base, int64_t N, int64_t M, int64_t P,
 }
 
 cudaError_t launch_tsqr_fp64(const TsqrState& s, const void* X, int64_t ldx, int xtype,
-                             const double* w, int remove_mean, double* mean, cudaStream_t st) {
+                             const double* w, int remove_mean, double* mean, cudaStream_t st, cudaEvent_t mid) {
   cudaError_t e;
   if ((e = ensure_dyn_smem((const void*)leaf_qr_kernel, kLeafSmemBytes)) != cudaSuccess) return e;
   if ((e = ensure_dyn_smem((const void*)modes_kernel, kLeafSmemBytes)) != cudaSuccess) return e;
   LeafArgs a{s, X, ldx, xtype, w, remove_mean, mean};
   leaf_qr_kernel<<<(unsigned)s.Pl, kLeafThreads, kLeafSmemBytes, st>>>(a);
   e = cudaGetLastError();
+  if (e == cudaSuccess && mid) e = cudaEventRecord(mid, st);
   // a launch over a slice of the leaves (streamed) leaves the cooperative
   // tree to its caller, after the last slice
   if (e != cudaSuccess || s.climb || s.Pl != s.P) return e;

@@ -1068,7 +1068,7 @@ static cudaError_t encode_yf_map(CUtensorMap* map, float* Yf, int64_t N, int64_t
 }
 
 cudaError_t launch_tsqr_mixed(const TsqrState& s, char* extra, const void* X, int64_t ldx, int xtype,
-                              const double* w, int remove_mean, double* mean, cudaStream_t st) {
+                              const double* w, int remove_mean, double* mean, cudaStream_t st, cudaEvent_t mid) {
   cudaError_t e;
   if ((e = ensure_dyn_smem((const void*)leaf_qr_mixed_kernel, kMixSmemTotal)) != cudaSuccess) return e;
   if ((e = ensure_dyn_smem((const void*)modes_mixed_kernel, kMixSmemTotal)) != cudaSuccess) return e;
@@ -1081,6 +1081,7 @@ cudaError_t launch_tsqr_mixed(const TsqrState& s, char* extra, const void* X, in
   if ((e = encode_yf_map(&tmV, a.Yf, s.N, s.M, kNB2)) != cudaSuccess) return e;
   leaf_qr_mixed_kernel<<<(unsigned)s.P, kMxThreads, kMixSmemTotal, st>>>(a, tmC, tmV);
   e = cudaGetLastError();
+  if (e == cudaSuccess && mid) e = cudaEventRecord(mid, st);
   if (e != cudaSuccess || s.climb) return e;
   return launch_tree_coop(s, st);
 }
