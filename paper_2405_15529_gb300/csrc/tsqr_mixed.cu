@@ -493,6 +493,24 @@ __device__ __forceinline__ void issue_3xtf32(uint32_t d_hh, uint32_t d_x, unsign
   }
 }
 
+// The W stage's 3xTF32 product in two MMAs per K-slice: the B tile holds
+// the hi rows (reflectors 0..31) followed by the lo rows (32..63), so one
+// N = 64 MMA gives hi*hi (accumulator columns 0..31) and hi*lo (32..63), and
+// an N = 32 MMA gives lo*hi into d_x2 (two MMAs of 3xTF32 work per K-slice
+// instead of three).
+__device__ __forceinline__ void issue_w_3xtf32(uint32_t d_wide, uint32_t d_x2, unsigned char* smem, int Kk) {
+  using namespace tc05;
+  const uint32_t a_hi = smem_u32(smem + kOffWA), a_lo = smem_u32(smem + kOffWAlo);
+  const uint32_t b_hi = smem_u32(smem + kOffWB);
+  static_assert(kOffWBlo == kOffWB + kWB, "the lo rows of B follow its hi rows");
+  const uint32_t sbo = (uint32_t)(Kk / 4) * 128, lbo = 128;
+  for (int kk = 0; kk < Kk / 8; ++kk) {
+    const uint32_t o = (uint32_t)kk * 256;
+    mma_tf32(d_wide, desc(a_hi + o, lbo, sbo), desc(b_hi + o, lbo, sbo), idesc_tf32(128, 2 * kNB2), kk > 0);
+    mma_tf32(d_x2, desc(a_lo + o, lbo, sbo), desc(b_hi + o, lbo, sbo), idesc_tf32(128, kNB2), kk > 0);
+  }
+}
+
 // The block-reflector application on tcgen05.  C: leaf-relative FP32 matrix
 // (rows r0..h, ld ldc), ncols columns.  TRANS: op(T) = T^T (factorisation) or
 // T (modes).  Returns false on a timed-out wait.
@@ -548,12 +566,13 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
       phase ^= 1u;
       fence_after();
       if (__syncthreads_or(!w_ok)) return false;
-      float hh[16], xx[16];
+      float hh[16], x1[16], x2[16];
       tmem_ld16(tmem + lanebase + (uint32_t)(16 * half), hh);
-      tmem_ld16(tmem + lanebase + (uint32_t)(kNB2 + 16 * half), xx);
+      tmem_ld16(tmem + lanebase + (uint32_t)(kNB2 + 16 * half), x1);
+      tmem_ld16(tmem + lanebase + (uint32_t)(2 * kNB2 + 16 * half), x2);
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        const float y = (hh[j] + xx[j]) - wc_[j];
+        const float y = (hh[j] + (x1[j] + x2[j])) - wc_[j];
         const float t = ws_[j] + y;
         wc_[j] = (t - ws_[j]) - y;
         ws_[j] = t;
@@ -654,7 +673,7 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
         fence_after();
         if (tid == 0) {
           if (kc + 2 < nkt) issue(kc + 2);
-          issue_3xtf32(tmem, tmem + kNB2, smem, kOffWA, kOffWAlo, kOffWB, kOffWBlo, kKC, idesc_tf32(128, kNB2));
+          issue_w_3xtf32(tmem, tmem + 2 * kNB2, smem, kKC);
           commit(mbar);
         }
         if (kc + 2 < nkt) ++issued;
@@ -712,7 +731,7 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
         __syncthreads();
         fence_after();
         if (tid == 0) {
-          issue_3xtf32(tmem, tmem + kNB2, smem, kOffWA, kOffWAlo, kOffWB, kOffWBlo, kKC, idesc_tf32(128, kNB2));
+          issue_w_3xtf32(tmem, tmem + 2 * kNB2, smem, kKC);
           commit(mbar);
         }
         if (kc + 1 < nkc) load_w(kc + 1);   // in flight while the MMAs run
