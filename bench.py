@@ -735,7 +735,11 @@ def bench_spod(args, dev):
     torch.cuda.synchronize()
     prec = pg.PREC_MIXED_3XTF32
     t_tune = time.perf_counter()
-    leaf_rows = tune.leaf_rows_for(Ns, Nbs, prec, tune=args.tune)
+    tune_times = None
+    if args.tune:
+        leaf_rows, tune_times = tune.tune_batched_workload(Q, 8, prec)
+    else:
+        leaf_rows = [0] * len(Q)
     t_tune = time.perf_counter() - t_tune
     b = pg.BatchedSVD(Q, kmodes=8, prec=prec, leaf_rows=leaf_rows)
     b.capture()
@@ -771,6 +775,7 @@ def bench_spod(args, dev):
                         "hbm_gbs_of_algorithmic_bytes": (in_bytes + out_bytes) / (ms * 1e-3) / 1e9},
            "sigma_err_vs_oracle_smallest_bins": errs,
            "leaf_rows_tuned": bool(args.tune), "tune_seconds_untimed": t_tune,
+           "tuned_policy_seconds": tune_times,
            "leaf_rows_histogram": {str(h): leaf_rows.count(h) for h in sorted(set(leaf_rows))}}
     del Q, b
     torch.cuda.empty_cache()

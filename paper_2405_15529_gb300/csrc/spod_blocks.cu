@@ -178,21 +178,35 @@ __global__ void __launch_bounds__(kFThreads) spod_dft_tc_kernel(const TD* D, int
   const float muf = (float)mu;
   const int64_t nfreq = npwin / 2 + 1;
   bool ok = true;
+  // FP32 input: the samples of block bb (row p of A: samples i0 .. i0 +
+  // npwin - 1, zeros in the K padding) are loaded into registers one block
+  // ahead, so their latency overlaps the previous block's MMAs and epilogue
+  // (a binary64 block would need twice the registers: it is loaded in place)
+  constexpr bool kAhead = sizeof(TD) == 4;
+  float xn[kAhead ? kFK : 1];
+  auto load_block = [&](int64_t bb) {
+    if constexpr (kAhead) {
+      const int64_t i0 = bb * (npwin - nolap);
+#pragma unroll
+      for (int j = 0; j < kFK; ++j) xn[j] = (live && j < npwin) ? (float)D[p + (i0 + j) * ldd] : 0.f;
+    }
+  };
+  load_block(0);
   for (int64_t b = 0; b < nblks && ok; ++b) {
-    const int64_t i0 = b * (npwin - nolap);
-    // A row p: samples i0 .. i0 + npwin - 1 (zeros in the K padding), split
-#pragma unroll 4
-    for (int j = 0; j < kFK; ++j) {
-      float x = 0.f;
-      if (live && j < npwin) {
-        if constexpr (sizeof(TD) == 4) x = D[p + (i0 + j) * ldd] - muf;
-        else x = (float)(D[p + (i0 + j) * ldd] - mu);
-      }
+    auto stage = [&](int j, float x) {
       float hi, lo;
       split_tf32(x, hi, lo);
       const uint32_t o = cm_off(tid, j, kFK);
       *(float*)(fsm + o) = hi;
       *(float*)(fsm + kFA + o) = lo;
+    };
+    if constexpr (kAhead) {
+#pragma unroll
+      for (int j = 0; j < kFK; ++j) stage(j, (live && j < npwin) ? xn[j] - muf : 0.f);
+    } else {
+      const int64_t i0 = b * (npwin - nolap);
+#pragma unroll 4
+      for (int j = 0; j < kFK; ++j) stage(j, (live && j < npwin) ? (float)(D[p + (i0 + j) * ldd] - mu) : 0.f);
     }
     fence_smem_async();
     fence_before();
@@ -211,6 +225,7 @@ __global__ void __launch_bounds__(kFThreads) spod_dft_tc_kernel(const TD* D, int
       }
       commit(&mbar);
     }
+    if (b + 1 < nblks) load_block(b + 1);
     const bool w_ok = mbar_wait(&mbar, phase);
     phase ^= 1u;
     fence_after();

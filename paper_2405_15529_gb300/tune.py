@@ -5,7 +5,12 @@ QR's memory traffic (a taller leaf streams its trailing columns from HBM once
 per reflector) against the binary64 tree (P - 1 merges of (8/3) Nb^3 real
 flops each).  For every (Nb class, N class) the tuner times a small batch of
 seeded sample bins with each candidate height through the library's own
-batched launch and keeps the fastest.
+batched launch and keeps the fastest.  Those per-class heights are tuned
+on a few bins at a time; inside a full launch of hundreds of bins the device
+is already busy and shorter leaves mostly add tree merges (on the 256-bin
+SPOD workload the per-class heights ran 2.80 s against 2.00 s for the
+built-in choice), so `tune_batched_workload` chooses among whole-batch
+policies timed on the batch itself, and the benchmark uses it.
 
 POD (pylom_pod): the leaf count P trades the leaves' parallelism (one or two
 thread blocks per SM) and their panel latency against the tree's (P - 1)
@@ -131,6 +136,46 @@ def leaf_rows_for(Ns, Nbs, prec: int, tune: bool = False):
     if dirty:
         _save(cache)
     return out
+
+
+def tune_batched_workload(Q, kmodes: int, prec: int, heights=(512, 768, 1024), reps: int = 1):
+    """Leaf heights for a whole batch, chosen on the batch itself.
+
+    A height that wins for a few bins of one size class can lose inside the
+    full persistent launch: with hundreds of bins the device is already
+    full, and shorter leaves only add binary64 tree merges.  So the policies
+    are timed on the actual bins, one launch each: the library's built-in
+    choice and one height for every bin (each of `heights`, at least the
+    bin's columns, at most the longest leaf of the precision).  Returns
+    (per-bin heights of the fastest policy, 0 = built-in; {policy: seconds})."""
+    import torch
+    hmax = pg.batched_max_leaf_rows(prec)
+    Nbs = [int(q.shape[1]) for q in Q]
+    policies = {"built-in": [0] * len(Q)}
+    for h in heights:
+        if h <= hmax:
+            policies[f"all {h}"] = [max(h, nb) for nb in Nbs]
+    times = {}
+    for name, lr in policies.items():
+        b = pg.BatchedSVD(Q, kmodes=kmodes, prec=prec, leaf_rows=lr)
+        b.run()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b.run()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        st = b.status()
+        if st != pg.OK:
+            raise pg.PylomError(st, f"autotuner batch run ({name})")
+        times[name] = min(ts)
+        del b
+        torch.cuda.empty_cache()
+    best = min(times, key=times.get)
+    return policies[best], times
 
 
 # ---------------------------------------------------------------------------

@@ -109,3 +109,19 @@ def test_pod_tuner_picks_fastest_and_result_holds(tmp_path, monkeypatch):
     assert times and times[best] == min(times.values())
     assert tune.pod_leaf_rows_for(N, M, pg.PREC_FP64, tune=True) in times
     assert pg.leaf_count(N, M, best) == N // best
+
+
+@pytest.mark.gpu
+def test_batched_workload_tuner_picks_fastest_policy():
+    torch = pytest.importorskip("torch")
+    import synth
+    Ns, Nbs = [30000, 9000, 70000], [40, 100, 17]
+    Q = [synth.spod_bin_torch(N, Nb, 60 + i, device="cuda").t() for i, (N, Nb) in enumerate(zip(Ns, Nbs))]
+    heights, times = tune.tune_batched_workload(Q, 4, pg.PREC_MIXED_3XTF32)
+    assert "built-in" in times and len(times) >= 2
+    best = min(times, key=times.get)
+    expect = [0] * 3 if best == "built-in" else [max(int(best.split()[1]), nb) for nb in Nbs]
+    assert heights == expect
+    b = pg.BatchedSVD(Q, kmodes=4, prec=pg.PREC_MIXED_3XTF32, leaf_rows=heights)
+    b.run()
+    assert b.status() == pg.OK
