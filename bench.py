@@ -1048,7 +1048,9 @@ def run_case(name: str) -> int:
                   phases printed;
     mixedwave512  two mixed-precision POD calls on a 1,048,576 x 512 wave field (same recipe);
     fp64ks        two binary64 POD calls on the 262,144 x 256 known-spectrum matrix (weights, 99 %,
-                  256 leaves), the small case of the benchmark workload's leaf and modes kernels."""
+                  256 leaves), the small case of the benchmark workload's leaf and modes kernels;
+    spodfront     two SPOD front-end calls on a 262,144 x 4128 float32 wave field (windows of 64
+                  instants overlapping by 32: 128 blocks, 33 frequencies)."""
     import torch
     import paper_2405_15529_gb300 as pg
     import synth
@@ -1056,6 +1058,16 @@ def run_case(name: str) -> int:
     if name == "spod16":
         out = bench_spod(argparse.Namespace(spod_bins=16, spod_steps=1, tune=False, warmup=1), dev)
         print("ms", round(out["ms_per_step"], 1), out["status"])
+        return 0
+    if name == "spodfront":
+        N, T, npwin, nolap = 1 << 18, 4128, 64, 32
+        XT = synth.waves_torch(N, T, 8, "geometric", 1e-3, 12, dev, dtype=torch.float32, row_chunk=1 << 18)
+        D = XT.t()
+        Q = None
+        for _ in range(2):
+            Q = pg.spod_blocks(D, npwin, nolap, True, Q=Q)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": name, "N": N, "T": T, "npwin": npwin, "nolap": nolap}))
         return 0
     if name == "fp64ks":
         N, M = 1 << 18, M_FULL
@@ -1113,7 +1125,7 @@ def main():
     ap.add_argument("--spod-bins", type=int, default=256)
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="run the SPOD bins with the built-in leaf heights instead of the autotuned ones")
-    ap.add_argument("--case", choices=["spod16", "mixed1808", "mixedwave512", "fp64ks"], default=None,
+    ap.add_argument("--case", choices=["spod16", "mixed1808", "mixedwave512", "fp64ks", "spodfront"], default=None,
                     help="run one fixed workload for a kernel capture instead of the benchmark")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
