@@ -31,7 +31,7 @@ METRIC = "POD GB/s of X processed"
 # workload (304 leaves), from a one-pass ncu capture of that launch inside
 # this benchmark (dram__bytes_read.sum + dram__bytes_write.sum); see the
 # profile summary of the FP64 path.
-LEAF_FP64_TRAFFIC_BYTES = 420.31e9 + 155.16e9
+LEAF_FP64_TRAFFIC_BYTES = 419.94e9 + 155.11e9
 LEAF_FP64_TRAFFIC_SOURCE = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:leaf_qr_kernel, "
                             "full-size launch (1 pass), profiles/pod_fp64_known_spectrum_4194304x256.md")
 N_FULL, M_FULL, ENERGY = 1 << 22, 256, 0.99
@@ -868,9 +868,13 @@ def run_ours(args, rank, world, local_rank):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     pg.profile_begin(args.steps)
+    # an event between consecutive steps as well, for the median step
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps - 1)]
     e0.record(stream)
-    for _ in range(args.steps):
+    for i in range(args.steps):
         step()
+        if i + 1 < args.steps:
+            evs[i].record(stream)
     e1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -878,6 +882,34 @@ def run_ours(args, rank, world, local_rank):
     phases, ncalls = pg.profile_end()
     clk = clocks.stop()
     ms = rank_max(e0.elapsed_time(e1) / args.steps, dev)
+    marks = [e0] + evs + [e1]
+    step_ms = sorted(marks[i].elapsed_time(marks[i + 1]) for i in range(args.steps))
+    median_ms = step_ms[len(step_ms) // 2] if len(step_ms) % 2 else 0.5 * (
+        step_ms[len(step_ms) // 2 - 1] + step_ms[len(step_ms) // 2])
+
+    # the same call captured in a CUDA graph and replayed (outside the timed region)
+    graph_ms = None
+    try:
+        gs = torch.cuda.Stream()
+        gs.wait_stream(stream)
+        with torch.cuda.stream(gs):
+            step()
+        gs.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=gs):
+            step()
+        graph.replay()
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record()
+        for _ in range(args.steps):
+            graph.replay()
+        g1.record()
+        torch.cuda.synchronize()
+        graph_ms = g0.elapsed_time(g1) / args.steps
+        del graph
+    except RuntimeError as exc:     # reported, not fatal: the eager number above is the result
+        graph_ms = f"capture failed: {exc}"
     bytes_x = N * M * 8
     value = job_gbs(bytes_x, ms, world)
 
@@ -997,6 +1029,10 @@ def run_ours(args, rank, world, local_rank):
     if world == 1 and not args.no_c3:
         extra["mixed_waves_1808"] = bench_waves_1808(args, dev)
 
+    tree_env = os.environ.get("PYLOM_TREE", "")
+    tree_kernel = ("tree_coop_kernel (level by level, merges spread over all blocks)"
+                   if tree_env == "coop" or (tree_env != "pipe" and M >= 384)
+                   else "tree_pipe_kernel (column-block pipeline, one block per merge)")
     levels = max(0, math.ceil(math.log2(P))) if P > 1 else 0
     launches_per_step = 1 + 3 + 1 + levels + 1   # leaf+tree, jacobi init/sweeps/finalize, root, tree levels, modes
     if rank == 0:
@@ -1022,7 +1058,7 @@ def run_ours(args, rank, world, local_rank):
                                         "independent chains (bench_probe.cu; MEASURED_PEAKS.json has no "
                                         "FP64 figure); cross-checked by the FP64 4096^3 product",
                          "algorithmic_flops_per_launch": flops_leaf, "ms_per_launch": leaf_ms,
-                         "tree": {"kernel": "tree_coop_kernel", "ms_per_launch": tree_ms,
+                         "tree": {"kernel": tree_kernel, "ms_per_launch": tree_ms,
                                   "algorithmic_flops_per_launch": flops_tree,
                                   "achieved_tflops": flops_tree / (tree_ms * 1e-3) / 1e12 if coop_tree else None}},
             "pct_roofline_pod": {"value": pct_roof,
@@ -1031,6 +1067,10 @@ def run_ours(args, rank, world, local_rank):
                                  "fp64_fma_tflops": peak_fma,
                                  "fp64_matmul_4096cubed_tflops": mm_tflops},
             "phases_ms_per_step": {k: v / max(ncalls, 1) for k, v in phases.items()},
+            "step_timing": {"mean_ms": ms, "median_ms": median_ms, "min_ms": step_ms[0], "max_ms": step_ms[-1],
+                            "graph_replay_ms": graph_ms,
+                            "graph_note": "one pylom_pod call captured in a CUDA graph, replayed "
+                                          "args.steps times after the timed region"},
             "accuracy": {"sigma_max_abs_err_over_smax_vs_closed_form": sig_err, "r": r,
                          "jacobi_sweeps": sweeps},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
@@ -1050,7 +1090,8 @@ def run_case(name: str) -> int:
     fp64ks        two binary64 POD calls on the 262,144 x 256 known-spectrum matrix (weights, 99 %,
                   256 leaves), the small case of the benchmark workload's leaf and modes kernels;
     spodfront     two SPOD front-end calls on a 262,144 x 4128 float32 wave field (windows of 64
-                  instants overlapping by 32: 128 blocks, 33 frequencies)."""
+                  instants overlapping by 32: 128 blocks, 33 frequencies), then three timed calls
+                  with and three without the mean removal."""
     import torch
     import paper_2405_15529_gb300 as pg
     import synth
@@ -1067,7 +1108,16 @@ def run_case(name: str) -> int:
         for _ in range(2):
             Q = pg.spod_blocks(D, npwin, nolap, True, Q=Q)
         torch.cuda.synchronize()
-        print(json.dumps({"case": name, "N": N, "T": T, "npwin": npwin, "nolap": nolap}))
+        out = {"case": name, "N": N, "T": T, "npwin": npwin, "nolap": nolap}
+        for rm in (True, False):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                pg.spod_blocks(D, npwin, nolap, rm, Q=Q)
+            e1.record()
+            torch.cuda.synchronize()
+            out["ms_remove_mean" if rm else "ms_no_mean"] = e0.elapsed_time(e1) / 3
+        print(json.dumps(out))
         return 0
     if name == "fp64ks":
         N, M = 1 << 18, M_FULL

@@ -458,7 +458,9 @@ pylom_status pylom_matmul(int transA, const double* A, const double* B, double* 
  * A host code that owns all device buffers through its own allocator, or a
  * loop that may not allocate once running, passes only R and the outputs;
  * the scratch is a fixed array inside the library (about 1 MiB per device
- * that loads it, held until the process exits).
+ * that loads it, held until the process exits).  The binary64 sweeps start
+ * from R^T: this entry point skips the binary32 preconditioning that
+ * pylom_svd_small runs from M = 256 on (same SVD, more sweeps).
  *  R, U, S, VT, ldr, ldu, ldvt, max_sweeps   as pylom_svd_small.
  *  M      1 <= M <= 256; larger M returns PYLOM_ERR_SHAPE (use
  *         pylom_svd_small with a workspace).

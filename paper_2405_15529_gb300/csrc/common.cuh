@@ -110,6 +110,29 @@ __device__ __forceinline__ void block_sum16(double (&v)[16], double* scratch, do
 }
 
 // Loads that bypass L1: data written by other blocks of the same launch.
+// Knuth's TwoSum in binary32: s = fl(a + b) and e with a + b = s + e
+// exactly (round-to-nearest intrinsics, so no contraction or reordering)
+__device__ __forceinline__ void two_sum32(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// sum of K binary32 values as the unevaluated pair s + c: every addition's
+// rounding error is carried in c, so s + c equals the exact sum up to a
+// second-order term of about ((K - 1) eps32)^2 times the sum of magnitudes
+template <int K>
+__device__ __forceinline__ void sum32_compensated(const float (&x)[K], float& s, float& c) {
+  s = 0.f;
+  c = 0.f;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    float e;
+    two_sum32(s, x[j], s, e);
+    c = __fadd_rn(c, e);
+  }
+}
+
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 
 // Grid-wide barrier for a cooperative launch (all blocks co-resident).
@@ -128,6 +151,10 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
 
 // `expected` is the number of arrivals that releases the barrier (the grid

@@ -9,11 +9,15 @@ namespace pylom {
 
 // Householder panel width of the FP64 leaf QR (two 8-row DMMA tiles).
 constexpr int kNB = 16;
-// From this many columns, or this many leaves, on, the tree merges run in
-// tree_coop_kernel.
+// Below kCoopTreeMinP leaves and kCoopTreeMinM columns the tree merges run
+// inside the leaf kernel (last-arriver climb); from kCoopTreeMinP leaves on
+// at fewer columns, in the column-block pipeline of tree_pipe_kernel; from
+// kCoopTreeMinM columns on, in tree_coop_kernel.
 constexpr int64_t kCoopTreeMinM = 384;
 constexpr int64_t kCoopTreeMinP = 64;
 bool use_climb_tree(int64_t M, int64_t P);
+bool use_pipe_tree(int64_t M, int64_t P);
+
 
 // Device pointers of one TSQR (+ modes) problem, carved from a workspace.
 struct TsqrState {
@@ -28,8 +32,10 @@ struct TsqrState {
   unsigned* arrive;         // P arrival counters of the tree merges
   double* B;                // P x M x rmax down-pass blocks (nullable if no modes)
   int64_t rmax;
-  double* Tt;               // 2 x ceil(P/2) x kNB x kNB: panel T factors of the cooperative tree
-  int climb;                // 1: leaves run the last-arriver tree; 0: tree_coop_kernel follows them
+  double* Tt;               // 2 x ceil(P/2) x kNB x kNB: panel T factors in flight in the cooperative tree
+  double* Tn;               // P x npan x kNB x kNB: panel T factors of the pipelined tree (by right child)
+  int climb;                // 1: leaves run the last-arriver tree; 0: a tree kernel follows them
+  int pipe;                 // with climb == 0: 1 tree_pipe_kernel, 0 tree_coop_kernel
   // leaf kernels of a streamed problem run on a slice of the leaves whose
   // rows sit in a device chunk: leaves leaf0 .. leaf0 + Pl - 1, buffer row 0
   // = global row row0, Y (and X, w, mean, U) chunks with leading dimension
@@ -53,8 +59,9 @@ struct SvdState {
 };
 
 // From this size on, binary32 block-Jacobi sweeps precondition the binary64
-// one-sided Jacobi of the small SVD (svd_jacobi32.cu).
-constexpr int64_t kJac32MinM = 512;
+// one-sided Jacobi of the small SVD (svd_jacobi32.cu).  At M = 256 they
+// take the SVD from 20.3 to 16.9 ms (11 binary64 sweeps before).
+constexpr int64_t kJac32MinM = 256;
 size_t jacobi32_extra_bytes(int64_t M);
 void jacobi32_carve(SvdState& s, char* p);
 cudaError_t launch_jacobi32_precondition(const SvdState& s, const double* R, int64_t ldr, cudaStream_t st);
@@ -64,8 +71,10 @@ cudaError_t launch_jacobi32_precondition(const SvdState& s, const double* R, int
 size_t tsqr_state_bytes(int64_t N, int64_t M, int64_t P, int64_t rmax, bool with_y = true);
 void tsqr_state_carve(TsqrState& s, char* base, int64_t N, int64_t M, int64_t P, int64_t rmax,
                       bool with_y = true);
-size_t svd_state_bytes(int64_t M);
-void svd_state_carve(SvdState& s, char* base, int64_t M);
+// precond: room for (and use of) the binary32 preconditioning when M >=
+// kJac32MinM; without it the binary64 sweeps start from R^T
+size_t svd_state_bytes(int64_t M, bool precond = true);
+void svd_state_carve(SvdState& s, char* base, int64_t M, bool precond = true);
 
 // Leaf QR of every row block (with fused mean/weight prologue) and the
 // last-arriver tree reduction; the root R ends in Rs[0].
@@ -77,6 +86,10 @@ cudaError_t launch_tsqr_fp64(const TsqrState& s, const void* X, int64_t ldx, int
 // The tree reduction as one cooperative launch over all blocks (for large
 // M); runs after the leaf kernel when s.climb == 0.
 cudaError_t launch_tree_coop(const TsqrState& s, cudaStream_t st);
+// The tree reduction as a column-block pipeline, one block per merge.
+cudaError_t launch_tree_pipe(const TsqrState& s, cudaStream_t st);
+// launch_tree_pipe or launch_tree_coop as s.pipe says (s.climb == 0)
+cudaError_t launch_tree(const TsqrState& s, cudaStream_t st);
 
 // Copy the root R (upper triangle) into an M x M matrix with zeros below.
 cudaError_t launch_copy_root_r(const TsqrState& s, double* R, int64_t ldr, cudaStream_t st);

@@ -201,7 +201,7 @@ extern "C" pylom_status pylom_pod_rstack(const double* Rstack, int64_t G, int64_
         e = cudaGetLastError();
       }
     } else {
-      e = launch_tree_coop(ts, st);
+      e = launch_tree(ts, st);
     }
   }
   if (e == cudaSuccess) e = launch_svd_fp64(ss, ts.Rs, M, UR, M, S, VT, ldvt, 60, energy, r_max, st);

@@ -220,7 +220,7 @@ extern "C" pylom_status pylom_pod_streamed(const void* X, int64_t N, int64_t M, 
     if (e != cudaSuccess) return fail_cuda("reflector download");
   }
   // (a single chunk covers every leaf and its launch already ran the cooperative tree)
-  if (!ts.climb && sp.nchunks > 1 && (e = launch_tree_coop(ts, cs)) != cudaSuccess) return fail_cuda("tree");
+  if (!ts.climb && sp.nchunks > 1 && (e = launch_tree(ts, cs)) != cudaSuccess) return fail_cuda("tree");
   if ((e = launch_svd_fp64(ss, ts.Rs, M, UR, M, S, VT, ldvt, 60, energy, r_max, cs)) != cudaSuccess)
     return fail_cuda("small SVD");
   if ((e = launch_down_pass_fp64(ts, UR, M, -1, cs)) != cudaSuccess) return fail_cuda("top-down pass");

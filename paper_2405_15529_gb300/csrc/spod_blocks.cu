@@ -34,13 +34,39 @@ __global__ void spod_tables_kernel(float* tab, int64_t npwin) {
   }
 }
 
-template <typename TD>
-__global__ void spod_mean_kernel(const TD* D, int64_t N, int64_t T, int64_t ldd, double* mean) {
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int64_t t = 0; t < T; ++t) s += (double)D[p + t * ldd];
-    mean[p] = s / (double)T;
+// temporal mean of every point, binary64 accumulation (one thread per point)
+__global__ void spod_mean_kernel(const double* D, int64_t N, int64_t T, int64_t ldd, double* mean) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  double s = 0.0;
+  for (int64_t t = 0; t < T; ++t) s += D[p + t * ldd];
+  mean[p] = s / (double)T;
+}
+
+// binary32 input: chunks of kMeanChunk instants are summed in binary32 with
+// an error-free transformation (Knuth's TwoSum: the rounding error of every
+// addition is carried in c), and only the pair (s, c) of each chunk is
+// added in binary64.  The chunk sum is then exact up to a second-order term
+// (about (kMeanChunk eps32)^2 of the sum of magnitudes, 4e-12 here), while
+// the binary64 instruction count drops kMeanChunk-fold: on this GPU the
+// binary64 pipe, not the memory, set the time of a per-sample binary64 sum.
+constexpr int kMeanChunk = 32;
+__global__ void spod_mean_f32_kernel(const float* D, int64_t N, int64_t T, int64_t ldd, double* mean) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  const float* col = D + p;
+  double acc = 0.0;
+  int64_t t = 0;
+  for (; t + kMeanChunk <= T; t += kMeanChunk) {
+    float x[kMeanChunk];
+#pragma unroll
+    for (int j = 0; j < kMeanChunk; ++j) x[j] = col[(t + j) * ldd];
+    float s, c;
+    sum32_compensated(x, s, c);
+    acc += (double)s + (double)c;
   }
+  for (; t < T; ++t) acc += (double)col[t * ldd];
+  mean[p] = acc / (double)T;
 }
 
 // grid (ceil(N / kSpodThreads), nBlks); dynamic shared memory:
@@ -330,10 +356,11 @@ extern "C" pylom_status pylom_spod_blocks(const void* D, int64_t N, int64_t T, i
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && remove_mean) {
+    const unsigned mgrid = (unsigned)((N + 255) / 256);
     if (dtype == PYLOM_F32)
-      spod_mean_kernel<float><<<512, 256, 0, st>>>((const float*)D, N, T, ldd, mu);
+      spod_mean_f32_kernel<<<mgrid, 256, 0, st>>>((const float*)D, N, T, ldd, mu);
     else
-      spod_mean_kernel<double><<<512, 256, 0, st>>>((const double*)D, N, T, ldd, mu);
+      spod_mean_kernel<<<mgrid, 256, 0, st>>>((const double*)D, N, T, ldd, mu);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && remove_mean && mean) e = cudaMemcpyAsync(mean, mu, sizeof(double) * (size_t)N,

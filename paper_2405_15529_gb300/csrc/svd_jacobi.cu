@@ -21,13 +21,13 @@ namespace pylom {
 constexpr int kJacThreads = 256;
 constexpr int kFinThreads = 1024;
 
-size_t svd_state_bytes(int64_t M) {
+size_t svd_state_bytes(int64_t M, bool precond) {
   const int64_t Mp = M + (M & 1);
   return align256(sizeof(double) * (size_t)M * Mp) + align256(sizeof(double) * (size_t)Mp * Mp) +
-         jacobi32_extra_bytes(M);
+         (precond ? jacobi32_extra_bytes(M) : 0);
 }
 
-void svd_state_carve(SvdState& s, char* base, int64_t M) {
+void svd_state_carve(SvdState& s, char* base, int64_t M, bool precond) {
   s.M = M;
   s.Mp = M + (M & 1);
   s.A = (double*)base;
@@ -36,7 +36,7 @@ void svd_state_carve(SvdState& s, char* base, int64_t M) {
   s.A32 = s.V32 = nullptr;
   s.G = s.Tm = s.mmws = nullptr;
   s.rot32 = nullptr;
-  if (M >= kJac32MinM)
+  if (precond && M >= kJac32MinM)
     jacobi32_carve(s, (char*)s.V + align256(sizeof(double) * (size_t)s.Mp * s.Mp));
 }
 
@@ -290,7 +290,7 @@ cudaError_t launch_svd_fp64(const SvdState& s, const double* R, int64_t ldr, dou
                             double* S, double* VT, int64_t ldvt, int max_sweeps, double energy,
                             int64_t r_max, cudaStream_t st) {
   cudaError_t e;
-  if (s.M >= kJac32MinM) {
+  if (s.A32) {
     e = launch_jacobi32_precondition(s, R, ldr, st);
   } else {
     jacobi_init_kernel<<<64, 256, 0, st>>>(s, R, ldr);

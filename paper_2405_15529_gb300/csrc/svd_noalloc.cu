@@ -12,6 +12,9 @@
 //
 // Limits and rules:
 //   - M <= kNoAllocMaxM (256); larger M is rejected with PYLOM_ERR_SHAPE.
+//   - The binary64 sweeps start from R^T without the binary32
+//     preconditioning (whose scratch the array does not hold): the same
+//     SVD, in more sweeps than pylom_svd_small takes at M = 256.
 //   - The array is shared by every call in the process on that device and
 //     keeps the last call's contents.  Each call clears the parts that must
 //     start at zero (status word, grid-barrier counters, rotation counts)
@@ -77,10 +80,10 @@ extern "C" pylom_status pylom_svd_small_noalloc(const double* R, int64_t M, int6
   }
   // the layout the Jacobi kernels carve (padded columns, 256-byte aligned
   // arrays) must fit the fixed array for this M
-  if (sizeof(WsHeader) + svd_state_bytes(M) > kNoAllocBytes) {
+  if (sizeof(WsHeader) + svd_state_bytes(M, false) > kNoAllocBytes) {
     set_error_message("pylom_svd_small_noalloc: M = %lld needs %zu bytes of scratch, more than the %zu "
                       "the fixed array holds; use pylom_svd_small with a workspace",
-                      (long long)M, sizeof(WsHeader) + svd_state_bytes(M), kNoAllocBytes);
+                      (long long)M, sizeof(WsHeader) + svd_state_bytes(M, false), kNoAllocBytes);
     return PYLOM_ERR_SHAPE;
   }
   int dev = 0;
@@ -111,7 +114,7 @@ extern "C" pylom_status pylom_svd_small_noalloc(const double* R, int64_t M, int6
   cudaStream_t st = (cudaStream_t)stream;
   SvdState ss;
   ss.hdr = (WsHeader*)base;
-  svd_state_carve(ss, (char*)base + sizeof(WsHeader), M);
+  svd_state_carve(ss, (char*)base + sizeof(WsHeader), M, false);
   e = cudaMemsetAsync(ss.hdr, 0, sizeof(WsHeader), st);
   if (e != cudaSuccess) {
     set_error_message("pylom_svd_small_noalloc: header clear: %s", cudaGetErrorString(e));

@@ -63,10 +63,15 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, int count) {
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity,
                                           unsigned long long limit_ns = kWaitLimitNs) {
   const unsigned long long t0 = global_ns();
+  // suspend-time hint: a waiting thread sleeps in try_wait until the phase
+  // completes or the hint runs out, instead of spinning on issue slots that
+  // the block's other warps need (at most 1 ms, so the limit still holds)
+  const uint32_t hint_ns = (uint32_t)(limit_ns / 8 < 1000000ull ? limit_ns / 8 : 1000000ull);
   while (true) {
     uint32_t done;
-    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(done) : "r"(smem_u32(mbar)), "r"(parity) : "memory");
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+                 "selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done) : "r"(smem_u32(mbar)), "r"(parity), "r"(hint_ns) : "memory");
     if (done) return true;
     if (global_ns() - t0 > limit_ns) return false;
   }

@@ -295,17 +295,33 @@ __global__ void copy_root_kernel(TsqrState s, double* R, int64_t ldr) {
 
 // Which tree: the last-arriver climb inside the leaf kernel overlaps the
 // merges with leaves still running and wins while there are few leaves and
-// a merge is cheap; from kCoopTreeMinM columns or kCoopTreeMinP leaves on,
-// the merges of each level are spread over all blocks instead (the leaves
-// finish together, and the climb's top levels are single-block merges in
-// sequence: 4,194,304 x 256 with 304 leaves, leaf + tree 661 -> 643 ms).
-// The environment variable PYLOM_TREE ("climb" or "coop") overrides the
-// choice.
+// a merge is cheap.  From kCoopTreeMinP leaves on the leaves finish
+// together and the climb's top levels are single-block merges in sequence;
+// below kCoopTreeMinM columns the column-block pipeline (tree_pipe.cu) then
+// overlaps the levels instead, and from kCoopTreeMinM columns on, where one
+// merge is too much work for one block, the cooperative tree spreads every
+// merge over all blocks level by level.  The environment variable
+// PYLOM_TREE ("climb", "coop" or "pipe") overrides the choice.
+static const char* tree_env() { return getenv("PYLOM_TREE"); }
+
 bool use_climb_tree(int64_t M, int64_t P) {
-  const char* env = getenv("PYLOM_TREE");
+  const char* env = tree_env();
+  if (P <= 1) return true;
   if (env && strcmp(env, "climb") == 0) return true;
+  if (env && (strcmp(env, "coop") == 0 || strcmp(env, "pipe") == 0)) return false;
+  return M < kCoopTreeMinM && P < kCoopTreeMinP;
+}
+
+bool use_pipe_tree(int64_t M, int64_t P) {
+  if (use_climb_tree(M, P)) return false;
+  const char* env = tree_env();
+  if (env && strcmp(env, "pipe") == 0) return true;
   if (env && strcmp(env, "coop") == 0) return false;
-  return P <= 1 || (M < kCoopTreeMinM && P < kCoopTreeMinP);
+  return M < kCoopTreeMinM;
+}
+
+cudaError_t launch_tree(const TsqrState& s, cudaStream_t st) {
+  return s.pipe ? launch_tree_pipe(s, st) : launch_tree_coop(s, st);
 }
 
 size_t tsqr_state_bytes(int64_t N, int64_t M, int64_t P, int64_t rmax, bool with_y) {
@@ -318,6 +334,7 @@ size_t tsqr_state_bytes(int64_t N, int64_t M, int64_t P, int64_t rmax, bool with
   b += align256(sizeof(double) * (size_t)P * M);
   b += align256(sizeof(unsigned) * (size_t)P);
   b += align256(sizeof(double) * (size_t)2 * ((P + 1) / 2) * kSmT);
+  b += align256(sizeof(double) * (size_t)P * npan * kSmT);
   b += align256(sizeof(double) * (size_t)P * M * rmax);
   return b;
 }
@@ -337,8 +354,10 @@ void tsqr_state_carve(TsqrState& s, char* base, int64_t N, int64_t M, int64_t P,
   s.tau_tree = (double*)p; p += align256(sizeof(double) * (size_t)P * M);
   s.arrive = (unsigned*)p; p += align256(sizeof(unsigned) * (size_t)P);
   s.Tt = (double*)p;       p += align256(sizeof(double) * (size_t)2 * ((P + 1) / 2) * kSmT);
+  s.Tn = (double*)p;       p += align256(sizeof(double) * (size_t)P * s.npan * kSmT);
   s.B = rmax > 0 ? (double*)p : nullptr;
   s.climb = use_climb_tree(M, P) ? 1 : 0;
+  s.pipe = use_pipe_tree(M, P) ? 1 : 0;
   s.leaf0 = 0;
   s.Pl = P;
   s.row0 = 0;
@@ -357,7 +376,7 @@ cudaError_t launch_tsqr_fp64(const TsqrState& s, const void* X, int64_t ldx, int
   // a launch over a slice of the leaves (streamed) leaves the cooperative
   // tree to its caller, after the last slice
   if (e != cudaSuccess || s.climb || s.Pl != s.P) return e;
-  return launch_tree_coop(s, st);
+  return launch_tree(s, st);
 }
 
 cudaError_t launch_copy_root_r(const TsqrState& s, double* R, int64_t ldr, cudaStream_t st) {

@@ -880,6 +880,64 @@ __device__ void mixed_prologue(const MixedArgs& a, float* Y, int64_t ldy, int64_
   if (bad) raise_status(a.s.hdr, PYLOM_ERR_NONFINITE);
 }
 
+// Binary32 snapshots: the same Y without per-element binary64 work (on this
+// GPU two conversions, an add, a subtract and a multiply in the binary64
+// pipe per sample cost a fifth of the leaf kernel at M = 256).  The mean is
+// summed in chunks of kPro by compensated binary32 sums (sum32_compensated)
+// whose pairs are added in binary64; the binary64 mean and sqrt(w) are then
+// split into binary32 pairs (hi + lo, 48 significant bits), x - mean is
+// formed as d + e by TwoSum and the rest of the mean folded into e, and the
+// product with sqrt(w) is rounded once more by two FMAs: Y is within a few
+// units in the last place of fl32(sqrt(w) (x - mean)) in binary64.
+__device__ void mixed_prologue_f32(const MixedArgs& a, float* Y, int64_t ldy, int64_t r0, int64_t h) {
+  const float* X = (const float*)a.X;
+  const int64_t M = a.s.M;
+  int bad = 0;
+  for (int64_t i = threadIdx.x; i < h; i += blockDim.x) {
+    const int64_t n = r0 + i;
+    const float* xr = X + n;
+    constexpr int kPro = 16;
+    double xbar = 0.0;
+    if (a.remove_mean) {
+      double acc = 0.0;
+      for (int64_t m0 = 0; m0 < M; m0 += kPro) {
+        float xv[kPro];
+#pragma unroll
+        for (int u = 0; u < kPro; ++u) xv[u] = (m0 + u < M) ? xr[(m0 + u) * a.ldx] : 0.f;
+        float s, c;
+        sum32_compensated(xv, s, c);
+        acc += (double)s + (double)c;
+      }
+      xbar = acc / (double)M;
+    }
+    if (a.mean) a.mean[n] = xbar;
+    double sw = 1.0;
+    if (a.w) {
+      const double wn = a.w[n];
+      if (!(wn > 0.0) || !isfinite(wn)) bad = 1;
+      sw = sqrt(wn);
+    }
+    const float xh = (float)xbar, xl = (float)(xbar - (double)xh);
+    const float sh = (float)sw, sl = (float)(sw - (double)sh);
+    for (int64_t m0 = 0; m0 < M; m0 += kPro) {
+      float xv[kPro];
+#pragma unroll
+      for (int u = 0; u < kPro; ++u) xv[u] = (m0 + u < M) ? xr[(m0 + u) * a.ldx] : 0.f;
+#pragma unroll
+      for (int u = 0; u < kPro; ++u) {
+        if (m0 + u < M) {
+          if (!isfinite(xv[u])) bad = 1;
+          float d, e;
+          two_sum32(xv[u], -xh, d, e);
+          const float lo = __fsub_rn(e, xl);
+          Y[i + (m0 + u) * ldy] = __fmaf_rn(d, sh, __fmaf_rn(d, sl, __fmul_rn(lo, sh)));
+        }
+      }
+    }
+  }
+  if (bad) raise_status(a.s.hdr, PYLOM_ERR_NONFINITE);
+}
+
 __global__ void __launch_bounds__(kMxThreads) leaf_qr_mixed_kernel(MixedArgs a, const __grid_constant__ CUtensorMap tmC,
                                                                   const __grid_constant__ CUtensorMap tmV) {
   extern __shared__ __align__(128) unsigned char msm[];
@@ -896,7 +954,7 @@ __global__ void __launch_bounds__(kMxThreads) leaf_qr_mixed_kernel(MixedArgs a, 
   float* Y = a.Yf + r0;
   double* sT = (double*)(msm + kOffT);
   if (a.xtype == PYLOM_F32)
-    mixed_prologue<float>(a, Y, ldy, r0, h);
+    mixed_prologue_f32(a, Y, ldy, r0, h);
   else
     mixed_prologue<double>(a, Y, ldy, r0, h);
   if (tid == 0) {
@@ -1102,7 +1160,7 @@ cudaError_t launch_tsqr_mixed(const TsqrState& s, char* extra, const void* X, in
   e = cudaGetLastError();
   if (e == cudaSuccess && mid) e = cudaEventRecord(mid, st);
   if (e != cudaSuccess || s.climb) return e;
-  return launch_tree_coop(s, st);
+  return launch_tree(s, st);
 }
 
 cudaError_t launch_modes_mixed(const TsqrState& s, char* extra, const double* Ur, int64_t ldur, int64_t r_fixed,

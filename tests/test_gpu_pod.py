@@ -96,6 +96,42 @@ def test_pod_repeatable_and_leaf_invariant():
         parity.check_sigma(_np(c.S), S_ref)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pod_graph_replay_is_repeatable(prec):
+    """One pylom_pod call (leaves, the pipelined tree from 64 leaves, small
+    SVD, top-down pass, modes) captured in a CUDA graph: replays agree with
+    each other bit for bit and with the eager call."""
+    N, M = 1 << 18, 64
+    X = synth.waves(N, M, n_waves=8, noise=1e-3, seed=21)
+    dt = torch.float64 if prec == 0 else torch.float32
+    Xd = _dev(X).to(dt)
+    res = pg.pod(Xd, energy=0.99, prec=prec)
+    assert pg.leaf_count(N, M, 0) >= 64
+    ws = res.workspace
+    U = pg.empty_colmajor(N, M, dt, "cuda")
+    S = torch.empty(M, dtype=torch.float64, device="cuda")
+    VT = pg.empty_colmajor(M, M, torch.float64, "cuda")
+    mean = torch.empty(N, dtype=torch.float64, device="cuda")
+    r_dev = torch.zeros(1, dtype=torch.int64, device="cuda")
+    out = (U, S, VT, mean, r_dev)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        pg.pod(Xd, energy=0.99, prec=prec, workspace=ws, out=out, stream=s, check=False)   # warm-up
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        pg.pod(Xd, energy=0.99, prec=prec, workspace=ws, out=out, stream=s, check=False)
+    g.replay()
+    torch.cuda.synchronize()
+    st, r, _ = pg.workspace_status(ws)
+    assert st == pg.OK and r == res.r
+    first = (U[:, :r].clone(), S.clone(), VT.clone())
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(first[0], U[:, :r]) and torch.equal(first[1], S) and torch.equal(first[2], VT)
+    assert torch.equal(S, res.S) and torch.equal(U[:, :r], res.U)
+
+
 def test_pod_zero_and_constant_rows():
     X = np.repeat(np.round(100 * np.random.default_rng(4).standard_normal((300, 1))), 12, axis=1)
     X = np.asfortranarray(X)

@@ -1,9 +1,10 @@
-"""GPU parity of the two forms of the tree reduction (Sec. 3.1, the reduce
-loop of Alg. 1): last-arriver merges inside the leaf kernels and the
-cooperative kernel that spreads every merge over all blocks (chosen with the
-PYLOM_TREE environment variable), each against the FP64 oracle, against each
-other, and through the top-down pass, the mixed path and the adjoint, which
-read the node reflectors both forms leave behind."""
+"""GPU parity of the three forms of the tree reduction (Sec. 3.1, the reduce
+loop of Alg. 1): last-arriver merges inside the leaf kernels, the
+cooperative kernel that spreads every merge over all blocks, and the
+column-block pipeline with one block per merge (chosen with the PYLOM_TREE
+environment variable), each against the FP64 oracle, against each other, and
+through the top-down pass, the mixed path and the adjoint, which read the
+node reflectors all three forms leave behind."""
 import functools
 import math
 
@@ -19,7 +20,7 @@ pytestmark = pytest.mark.gpu
 
 pg = pytest.importorskip("paper_2405_15529_gb300")
 
-TREES = ["climb", "coop"]
+TREES = ["climb", "coop", "pipe"]
 
 
 def _dev(X):
@@ -36,7 +37,7 @@ SHAPES = [
     (3001, 37, 128, True),       # P = 23, last panel short
     (5000, 10, 500, False),      # M below one panel
     (20000, 100, 1000, True),    # P = 20, seven panels
-    (1 << 20, 48, 0, True),      # automatic P = 304: nine levels, odd counts
+    (1 << 20, 48, 0, True),      # automatic P = 304: nine levels, odd counts; the pipeline by default
     (40000, 520, 2500, False),   # P = 16, 33 panels; the cooperative tree by default
 ]
 
@@ -66,9 +67,40 @@ def test_coop_tree_repeatable_and_agrees_with_climb(monkeypatch):
     assert np.max(np.abs(S - c.S.cpu().numpy())) <= 1e-13 * S[0]
 
 
-@pytest.mark.parametrize("N,M,b", [(3001, 37, 128), (1 << 18, 40, 0), (30000, 400, 3000)])
-def test_tsqr_coop_tree(monkeypatch, N, M, b):
+def test_pipe_tree_repeatable_and_agrees_with_coop(monkeypatch):
+    X, _ = _case(1 << 20, 48, True)
+    Xd = _dev(X)
+    monkeypatch.setenv("PYLOM_TREE", "pipe")
+    a = pg.pod(Xd, leaf_rows=0)
+    b = pg.pod(Xd, leaf_rows=0)
+    assert torch.equal(a.S, b.S) and torch.equal(a.U, b.U) and torch.equal(a.VT, b.VT)
     monkeypatch.setenv("PYLOM_TREE", "coop")
+    c = pg.pod(Xd, leaf_rows=0)
+    S = a.S.cpu().numpy()
+    assert np.max(np.abs(S - c.S.cpu().numpy())) <= 1e-13 * S[0]
+    parity.check_vectors(a.U.cpu().numpy(), c.U.cpu().numpy(), S, ncols=a.r)
+
+
+@pytest.mark.parametrize("P", [2, 3, 64, 65, 127, 300])
+def test_pipe_tree_leaf_counts(monkeypatch, P):
+    """Uneven trees: a missing partner passes R up, so a merge's bottom child
+    can be a leaf or a merge several levels down."""
+    monkeypatch.setenv("PYLOM_TREE", "pipe")
+    N, M = 40 * P + 17, 33
+    A = np.asfortranarray(np.random.default_rng(P).standard_normal((N, M)))
+    R, Q = pg.tsqr(_dev(A), leaf_rows=N // P)
+    R, Q = R.cpu().numpy(), Q.cpu().numpy()
+    nA = np.linalg.norm(A)
+    assert np.allclose(np.tril(R, -1), 0.0)
+    assert np.linalg.norm(R.T @ R - A.T @ A) <= 1e-13 * nA ** 2
+    assert np.linalg.norm(Q.T @ Q - np.eye(M)) <= 1e-13 * math.sqrt(M)
+    assert np.linalg.norm(Q @ R - A) <= 1e-13 * nA
+
+
+@pytest.mark.parametrize("tree", ["coop", "pipe"])
+@pytest.mark.parametrize("N,M,b", [(3001, 37, 128), (1 << 18, 40, 0), (30000, 400, 3000)])
+def test_tsqr_coop_tree(monkeypatch, tree, N, M, b):
+    monkeypatch.setenv("PYLOM_TREE", tree)
     A = np.asfortranarray(np.random.default_rng(N + M).standard_normal((N, M)))
     R, Q = pg.tsqr(_dev(A), leaf_rows=b)
     R, Q = R.cpu().numpy(), Q.cpu().numpy()
@@ -79,9 +111,10 @@ def test_tsqr_coop_tree(monkeypatch, N, M, b):
     assert np.linalg.norm(Q @ R - A) <= 1e-13 * nA
 
 
+@pytest.mark.parametrize("tree", ["coop", "pipe"])
 @pytest.mark.parametrize("N,M,b", [(3001, 37, 128), (40000, 520, 2500)])
-def test_mixed_path_coop_tree(monkeypatch, N, M, b):
-    monkeypatch.setenv("PYLOM_TREE", "coop")
+def test_mixed_path_coop_tree(monkeypatch, tree, N, M, b):
+    monkeypatch.setenv("PYLOM_TREE", tree)
     X, ref = _case(N, M, False)
     res = pg.pod(_dev(X.astype(np.float32)), remove_mean=False, leaf_rows=b, prec=pg.PREC_MIXED_3XTF32)
     S, S_ref = res.S.cpu().numpy(), ref["S"]
@@ -89,8 +122,9 @@ def test_mixed_path_coop_tree(monkeypatch, N, M, b):
     assert np.max(np.abs(S - S_ref)) <= 2e-6 * S_ref[0]
 
 
-def test_adjoint_through_coop_tree(monkeypatch):
-    monkeypatch.setenv("PYLOM_TREE", "coop")
+@pytest.mark.parametrize("tree", ["coop", "pipe"])
+def test_adjoint_through_coop_tree(monkeypatch, tree):
+    monkeypatch.setenv("PYLOM_TREE", tree)
     N, M, r = 512, 16, 4
     X, w, s = synth.known_spectrum(N, M, weights=True, seeds=(7, 8, 9))
     Xd = _dev(X).requires_grad_(True)
