@@ -1034,7 +1034,13 @@ def run_ours(args, rank, world, local_rank):
                    if tree_env == "coop" or (tree_env != "pipe" and M >= 384)
                    else "tree_pipe_kernel (column-block pipeline, one block per merge)")
     levels = max(0, math.ceil(math.log2(P))) if P > 1 else 0
-    launches_per_step = 1 + 3 + 1 + levels + 1   # leaf+tree, jacobi init/sweeps/finalize, root, tree levels, modes
+    # per POD call (counted in the ncu launch list of this command): leaf kernel, tree kernel
+    # (pipelined or cooperative; none when the leaves merge as they finish), the small SVD
+    # (binary32 preconditioning from M = 256: init, sweeps, widen, 2 Newton-Schulz steps of two
+    # products each + A = R^T V; else one init) + binary64 sweeps + finalize, the root block,
+    # one top-down launch per tree level, the modes
+    svd_launches = (3 + 5 + 2 if M >= 256 else 1) + 2
+    launches_per_step = 1 + (1 if P >= 64 or M >= 384 else 0) + svd_launches + 1 + levels + 1
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,

@@ -328,14 +328,27 @@ __device__ void hr_chunk_q(float* Y, int64_t ldy, int64_t k, int nbk, int64_t L,
     x[0][col] = Bc[lane * kNB2 + col];
     x[1][col] = x[2][col] = x[3][col] = 0.f;
   }
+  // reflector j's entries of this lane's rows, loaded two reflectors ahead
+  // of their use so the loads' latency overlaps the applications
+  auto load_v = [&](int j, float (&v)[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int64_t row = lane + 32 * q;
+      v[q] = (j < 0) ? 0.f : ((row == j) ? 1.f : ((row > j && row < nrow) ? Y[base + row + (k + j) * ldy] : 0.f));
+    }
+  };
+  float v1[4], v2[4];
+  load_v(nbk - 1, v1);
+  load_v(nbk - 2, v2);
 #pragma unroll 1
   for (int j = nbk - 1; j >= 0; --j) {
     float v[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int64_t row = lane + 32 * q;
-      v[q] = (row == j) ? 1.f : ((row > j && row < nrow) ? Y[base + row + (k + j) * ldy] : 0.f);
+      v[q] = v1[q];
+      v1[q] = v2[q];
     }
+    load_v(j - 2, v2);
     const float tau = tch[j];
     float pd[kNB2];
 #pragma unroll
@@ -386,6 +399,7 @@ __device__ void panel_tsqr_hr(float* Y, int64_t ldy, int64_t k, int nbk, int64_t
   float* sU = sf;                      // 32 x 33: U of the LU, then reused
   float* sR = sf + 32 * 33;            // 32 x 33: root R
   float* sS = sR + 32 * 33;            // 32 signs
+  float* sD = sS + 32;                 // 32 reciprocals of U's diagonal
   for (int idx = tid; idx < kNB2 * kNB2; idx += nthr) sR[(idx / kNB2) * 33 + idx % kNB2] = hs[idx];
   // B_0 = I
   for (int idx = tid; idx < kNB2 * kNB2; idx += nthr)
@@ -428,6 +442,7 @@ __device__ void panel_tsqr_hr(float* Y, int64_t ldy, int64_t k, int nbk, int64_t
     }
 #pragma unroll
     for (int r = 0; r < kNB2; ++r) sU[r * 33 + lane] = q[r];   // U on and above the diagonal, L1 below
+    sD[lane] = (lane < nbk) ? 1.f / q[lane] : 0.f;
   }
   __syncthreads();
   // V rows below the top block: y = x U^-1 (a thread per row)
@@ -441,7 +456,7 @@ __device__ void panel_tsqr_hr(float* Y, int64_t ldy, int64_t k, int nbk, int64_t
         float acc = y[j];
 #pragma unroll
         for (int l = 0; l < j; ++l) acc = fmaf(-y[l], sU[l * 33 + j], acc);
-        y[j] = acc / sU[j * 33 + j];
+        y[j] = acc * sD[j];
       }
     }
 #pragma unroll
