@@ -62,15 +62,17 @@ __device__ __forceinline__ double ld_c(const double* p) {
 // on the nbk rows top[0:nbk, 0:ncols] (ld ldtop): the tree-node case.
 // The contractions W = V^T C and C -= V W' run on the FP64 tensor pipe
 // (mma.sync m8n8k4); W is reduced over row slices in a fixed order, so
-// results are bitwise repeatable.  CG: load C through L2 only.
+// results are bitwise repeatable.  CG: load C through L2 only.  wr1 >= 0:
+// C is zero from row wr1 on, so W sums rows r0..wr1-1 only.
 template <bool TRANS, bool CG, class VF>
 __device__ void block_reflector(const VF& V, int nbk, int64_t r0, int64_t r1, double* C, int64_t ldc,
                                 int ncols, double* top, int64_t ldtop, const double* sT, double* sW,
-                                double* sWp) {
+                                double* sWp, int64_t wr1 = -1) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int64_t L = r1 - r0;
-  const int64_t nsteps = (L + 3) / 4;
+  const int64_t r1w = (wr1 >= r0 && wr1 < r1) ? wr1 : r1;   // rows of the W sums
+  const int64_t nsteps = (r1w - r0 + 3) / 4;
   for (int c0 = 0; c0 < ncols; c0 += kCW) {
     const int wc = min(kCW, ncols - c0);
     const int NT = (wc + 7) / 8;
@@ -88,7 +90,7 @@ __device__ void block_reflector(const VF& V, int nbk, int64_t r0, int64_t r1, do
         for (int tt = 0; tt < kTPW; ++tt) acc[mt][tt][0] = acc[mt][tt][1] = 0.0;
       for (int64_t stp = sb; stp < se; ++stp) {
         const int64_t row = r0 + stp * 4 + t;
-        const bool rok = row < r1;
+        const bool rok = row < r1w;
         const double a0 = rok ? V(row, g) : 0.0;
         const double a1 = rok ? V(row, 8 + g) : 0.0;
 #pragma unroll

@@ -26,72 +26,98 @@ namespace pylom {
 // Householder factorisation of the panel A[k:h, k:k+nbk] (Eq. svdqr1 on a
 // row block), textbook convention beta = -sign(alpha)|x|, sign(0) = +1.
 // Builds T (row-major kNB x kNB, upper) by the forward recurrence
-// T[0:j, j] = -tau_j T[0:j, 0:j] (V[:, 0:j]^T v_j).  Scalar FP64: each column
-// is one pass that scales v_j and forms its dot products with the panel,
-// then one pass that updates the panel (and the next column's norm).
+// T[0:j, j] = -tau_j T[0:j, 0:j] (V[:, 0:j]^T v_j).  Scalar FP64, one pass
+// over the panel rows per column: the pass of column j scales v_j, applies
+// reflector j to the later columns and, on the rows below j + 1, sums the
+// products of the updated column j + 1 with every panel column (reflectors
+// 0..j, itself, the later columns).  With those sums d_c, the dot products
+// reflector j + 1 needs are scale_{j+1} d_c + A[j+1, c] (its unit entry
+// meets row j + 1), so one block reduction per column serves the next
+// column's norm, its update and its T column.
+// Scratch: sred (block sums in [0, 16 nwarps), the next column's dot
+// products at kPdDot, its scalars at kPdScal), sout (block totals; tau_j
+// times the dot products at 16..31).
+constexpr int kPdDot = 256, kPdScal = 288;
 __device__ void panel_factor(double* A, int64_t lda, int64_t k, int nbk, int64_t h, double* tau_out,
                              double* sT, double* sred, double* sout) {
   const int tid = threadIdx.x, nthr = blockDim.x;
-  double xx;
-  {
-    double v[1] = {0.0};
-    for (int64_t i = k + 1 + tid; i < h; i += nthr) {
-      const double a = A[i + k * lda];
-      v[0] += a * a;
-    }
-    block_sum<1>(v, sred, sout);
-    xx = sout[0];
+  double* sdot = sred + kPdDot;     // v_j^T a_c (c != j)
+  double* sts = sout + kNB;         // tau_j v_j^T a_c
+  double acc[kNB];
+#pragma unroll
+  for (int c = 0; c < kNB; ++c) acc[c] = 0.0;
+  // column k: d_c = sum over rows below k of A[i, k] A[i, k + c] (c = 0: the norm)
+  for (int64_t i = k + 1 + tid; i < h; i += nthr) {
+    const double a0 = A[i + k * lda];
+#pragma unroll
+    for (int c = 0; c < kNB; ++c)
+      if (c < nbk) acc[c] += a0 * A[i + (k + c) * lda];
   }
+  block_sum16(acc, sred, sout);
   for (int jj = 0; jj < nbk; ++jj) {
     const int64_t j = k + jj;
-    const double alpha = A[j + j * lda];
-    double tau_j = 0.0, beta = alpha, scale = 0.0;
-    if (xx != 0.0) {
-      const double nrm = sqrt(alpha * alpha + xx);
-      beta = (alpha >= 0.0) ? -nrm : nrm;
-      tau_j = (beta - alpha) / beta;
-      scale = 1.0 / (alpha - beta);
+    // thread 0 forms the reflector's scalars and dot products (binary64
+    // square roots and divisions are slow on this part) and broadcasts them
+    if (tid == 0) {
+      const double alpha = A[j + j * lda], xx = sout[jj];
+      double tau_j = 0.0, beta = alpha, scale = 0.0;
+      if (xx != 0.0) {
+        const double nrm = sqrt(alpha * alpha + xx);
+        beta = (alpha >= 0.0) ? -nrm : nrm;
+        tau_j = (beta - alpha) / beta;
+        scale = 1.0 / (alpha - beta);
+      }
+      for (int c = 0; c < nbk; ++c) {
+        const double d = (c == jj) ? 0.0 : scale * sout[c] + A[j + (k + c) * lda];
+        sdot[c] = d;
+        sts[c] = tau_j * d;
+      }
+      sred[kPdScal] = tau_j;
+      sred[kPdScal + 1] = beta;
+      sred[kPdScal + 2] = scale;
+      tau_out[jj] = tau_j;
     }
-    double acc[kNB];
+    __syncthreads();
+    const double tau_j = sred[kPdScal], beta = sred[kPdScal + 1], scale = sred[kPdScal + 2];
+    // column jj of T, one row per thread (rows 0..jj-1)
+    if (tid < jj) {
+      double s = 0.0;
+      for (int q = tid; q < jj; ++q) s += sT[tid * kNB + q] * sdot[q];
+      sT[tid * kNB + jj] = -tau_j * s;
+    }
+    if (tid == 0) sT[jj * kNB + jj] = tau_j;
+    const bool more = jj + 1 < nbk;
 #pragma unroll
     for (int c = 0; c < kNB; ++c) acc[c] = 0.0;
     for (int64_t i = j + tid; i < h; i += nthr) {
-      double v = 1.0;
-      if (i != j) {
+      double v;
+      if (i == j) {
+        v = 1.0;
+        A[j + j * lda] = beta;
+      } else {
         v = A[i + j * lda] * scale;
         A[i + j * lda] = v;
       }
+      double row[kNB];
+#pragma unroll
+      for (int c = 0; c < kNB; ++c) row[c] = (c < nbk && c != jj) ? A[i + (k + c) * lda] : 0.0;
 #pragma unroll
       for (int c = 0; c < kNB; ++c)
-        if (c < nbk && c != jj) acc[c] += v * A[i + (k + c) * lda];
-    }
-    block_sum16(acc, sred, sout);
-    if (tid == 0) {
-      A[j + j * lda] = beta;
-      tau_out[jj] = tau_j;
-      for (int p = 0; p < jj; ++p) {
-        double s = 0.0;
-        for (int q = p; q < jj; ++q) s += sT[p * kNB + q] * sout[q];
-        sT[p * kNB + jj] = -tau_j * s;
-      }
-      sT[jj * kNB + jj] = tau_j;
-    }
-    double nx[1] = {0.0};
-    if (jj + 1 < nbk) {
-      for (int64_t i = j + tid; i < h; i += nthr) {
-        const double v = (i == j) ? 1.0 : A[i + j * lda];
-#pragma unroll
-        for (int c = 0; c < kNB; ++c) {
-          if (c > jj && c < nbk) {
-            const double a = A[i + (k + c) * lda] - tau_j * sout[c] * v;
-            A[i + (k + c) * lda] = a;
-            if (c == jj + 1 && i > j + 1) nx[0] += a * a;
-          }
+        if (c > jj && c < nbk) {
+          row[c] -= sts[c] * v;
+          A[i + (k + c) * lda] = row[c];
         }
+      if (more && i > j + 1) {
+        double a1 = 0.0;   // row[jj + 1], selected without indexing the array at run time
+#pragma unroll
+        for (int c = 1; c < kNB; ++c)
+          if (c == jj + 1) a1 = row[c];
+#pragma unroll
+        for (int c = 0; c < kNB; ++c)
+          if (c < nbk) acc[c] += a1 * ((c == jj) ? v : row[c]);
       }
     }
-    block_sum<1>(nx, sred, sout);
-    xx = sout[0];
+    if (more) block_sum16(acc, sred, sout);
   }
 }
 
@@ -269,7 +295,9 @@ __global__ void __launch_bounds__(kLeafThreads) modes_kernel(TsqrState s, int64_
     for (int idx = tid; idx < kSmT; idx += nthr) sT[idx] = Tg[idx];
     __syncthreads();
     LeafV V{A, s.ldy, k, h, nbk};
-    block_reflector<false, false>(V, nbk, k, h, C, ldu, (int)r, nullptr, 0, sT, sW, sWp);
+    // the first panel applied meets [B; 0]: its W sums only rows k..M-1
+    block_reflector<false, false>(V, nbk, k, h, C, ldu, (int)r, nullptr, 0, sT, sW, sWp,
+                                  pan == s.npan - 1 ? M : -1);
     __syncthreads();
   }
   if (physical && w) {

@@ -551,10 +551,12 @@ struct TmaW {
   uint32_t* tphase;
 };
 
+// wh >= 0 (register path): C is zero from leaf row wh on, so the W stage
+// sums rows k..wh-1 only.
 template <bool TRANS, bool TMA = false>
 __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int nbk, int64_t h, float* C,
                                    int64_t ldc, int ncols, const double* sT, unsigned char* smem, uint32_t tmem,
-                                   uint64_t* mbar, uint32_t& phase, TmaW tw = TmaW{}) {
+                                   uint64_t* mbar, uint32_t& phase, TmaW tw = TmaW{}, int64_t wh = -1) {
   using namespace tc05;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int quad = warp & 3, half = warp >> 2;       // tensor-memory lane quadrant; which half of the work
@@ -569,7 +571,8 @@ __device__ bool block_reflector_tc(const float* Y, int64_t ldy, int64_t k, int n
     float ws_[16], wc_[16];
 #pragma unroll
     for (int p = 0; p < 16; ++p) ws_[p] = wc_[p] = 0.f;
-    const int64_t nkc = (L + kKC - 1) / kKC;
+    const int64_t Lw = (!TMA && wh > k && wh < h) ? wh - k : L;
+    const int64_t nkc = (Lw + kKC - 1) / kKC;
     // staging map: warp instruction u of warp w covers core matrix u * 8 + w
     // of the operand (8 operand rows x 4 K elements, 128 contiguous bytes of
     // shared memory), so the split stores are free of bank conflicts; lane l
@@ -1057,7 +1060,9 @@ __global__ void __launch_bounds__(kMxThreads) modes_mixed_kernel(TsqrState s, co
     const double* Tg = T2 + (leaf * npan + pan) * kNB2 * kNB2;
     for (int idx = tid; idx < kNB2 * kNB2; idx += blockDim.x) sT[idx] = Tg[idx];
     __syncthreads();
-    ok = block_reflector_tc<false>(Y, yf_ld(s.N), k, nbk, h, C, ldu, (int)r, sT, msm, tmem, &mbar, phase);
+    // the first panel applied meets [B; 0]: its W stage sums rows k..M-1 only
+    ok = block_reflector_tc<false>(Y, yf_ld(s.N), k, nbk, h, C, ldu, (int)r, sT, msm, tmem, &mbar, phase, TmaW{},
+                                   pan == npan - 1 ? M : -1);
     __syncthreads();
   }
   tc05::fence_before();
