@@ -31,7 +31,7 @@ METRIC = "POD GB/s of X processed"
 # workload (304 leaves), from a one-pass ncu capture of that launch inside
 # this benchmark (dram__bytes_read.sum + dram__bytes_write.sum); see the
 # profile summary of the FP64 path.
-LEAF_FP64_TRAFFIC_BYTES = 419.94e9 + 155.11e9
+LEAF_FP64_TRAFFIC_BYTES = 345.47e9 + 153.50e9
 LEAF_FP64_TRAFFIC_SOURCE = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:leaf_qr_kernel, "
                             "full-size launch (1 pass), profiles/pod_fp64_known_spectrum_4194304x256.md")
 N_FULL, M_FULL, ENERGY = 1 << 22, 256, 0.99
