@@ -933,13 +933,17 @@ def run_ours(args, rank, world, local_rank):
     t_roof = max(bytes_x / (hbm_peak * 1e9), 2.0 * N * M * M / (peak_mma * 1e12))
     pct_roof = t_roof / (ms * 1e-3)
 
-    # end to end through the public API from pinned host memory
+    # end to end through the public API from pinned host memory: pylom_pod
+    # reads X where it lies (page-locked host memory, mapped into the
+    # device's address space) -- the leaf kernel's prologue loads cross the
+    # host link, so the transfer is part of the POD launch and overlaps its
+    # compute; the modes, S, VT and r come back by copies
     e2e = None
     if not args.no_e2e:
         Xh = host["X"]
         Xh.copy_(XT)
+        XhT = Xh.t()                          # column-major N x M view of the host buffer
         wh = w.cpu().pin_memory()
-        Xd = torch.empty_like(XT)
         wd = torch.empty_like(w)
         Uh = host["U"]
         Sh = torch.empty(M, dtype=torch.float64, pin_memory=True)
@@ -947,34 +951,36 @@ def run_ours(args, rank, world, local_rank):
         rh = torch.empty(1, dtype=torch.int64, pin_memory=True)
         d2h = 0
 
-        split = {"h2d": 0.0, "pod": 0.0, "d2h": 0.0}
+        split = {"w_h2d": 0.0, "pod_reading_host_x": 0.0, "d2h": 0.0}
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
 
-        def e2e_step(record=False):
+        def fetch_results():
             nonlocal d2h
-            if record:
-                ev[0].record()
-            pg.upload(Xd, Xh)                 # 256 MB pieces (one multi-GB copy runs at a fraction of the link)
-            wd.copy_(wh, non_blocking=True)
-            if record:
-                ev[1].record()
-            pg.pod(Xd.t(), w=wd, remove_mean=False, energy=ENERGY, r_max=M, leaf_rows=args.leaf_rows,
-                   workspace=ws, out=out, check=False)
-            if record:
-                ev[2].record()
             rh.copy_(r_dev, non_blocking=True)
             Sh.copy_(S, non_blocking=True)
             VTh.copy_(VT.t(), non_blocking=True)
             torch.cuda.current_stream().synchronize()
             rr = int(rh.item())
             Uh[:rr].copy_(U.t()[:rr], non_blocking=True)
+            d2h = 8 + M * 8 + M * M * 8 + rr * N * 8
+
+        def e2e_step(record=False):
+            if record:
+                ev[0].record()
+            wd.copy_(wh, non_blocking=True)
+            if record:
+                ev[1].record()
+            pg.pod(XhT, w=wd, remove_mean=False, energy=ENERGY, r_max=M, leaf_rows=args.leaf_rows,
+                   workspace=ws, out=out, check=False)
+            if record:
+                ev[2].record()
+            fetch_results()
             if record:
                 ev[3].record()
                 ev[3].synchronize()
-                split["h2d"] += ev[0].elapsed_time(ev[1])
-                split["pod"] += ev[1].elapsed_time(ev[2])
+                split["w_h2d"] += ev[0].elapsed_time(ev[1])
+                split["pod_reading_host_x"] += ev[1].elapsed_time(ev[2])
                 split["d2h"] += ev[2].elapsed_time(ev[3])
-            d2h = 8 + M * 8 + M * M * 8 + rr * N * 8
         e2e_step()
         torch.cuda.synchronize()
         if world > 1:
@@ -990,14 +996,38 @@ def run_ours(args, rank, world, local_rank):
         # one more step with events between its parts (outside the timed region)
         e2e_step(record=True)
         torch.cuda.synchronize()
+        S_e2e = Sh.clone()
+        # the other route, outside the timed region: copy X with the copy
+        # engines (256 MB pieces), then the POD of the device copy
+        Xd = torch.empty_like(XT)
+        c = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        copy_route = []
+        for _ in range(3):
+            c[0].record()
+            pg.upload(Xd, Xh)
+            wd.copy_(wh, non_blocking=True)
+            c[1].record()
+            pg.pod(Xd.t(), w=wd, remove_mean=False, energy=ENERGY, r_max=M, leaf_rows=args.leaf_rows,
+                   workspace=ws, out=out, check=False)
+            fetch_results()
+            c[2].record()
+            c[2].synchronize()
+            copy_route.append({"ms": c[0].elapsed_time(c[2]),
+                               "h2d_gbs": (N * M * 8 + N * 8) / (c[0].elapsed_time(c[1]) * 1e-3) / 1e9})
+        del Xd
         e2e = {"value": job_gbs(bytes_x, ems, world), "unit": "GB/s", "ms_per_step": ems,
                "h2d_bytes_per_step": N * M * 8 + N * 8, "d2h_bytes_per_step": d2h,
+               "route": "pylom_pod on the page-locked host X (read by the leaf kernel across the host link) "
+                        "+ 33.6 MB copy of w; U[:, :r], S, VT, r copied back",
                "split_ms_one_step": split, "host_buffers_pinned": bool(Xh.is_pinned() and Uh.is_pinned()),
-               "h2d_gbs_one_step": (N * M * 8 + N * 8) / (split["h2d"] * 1e-3) / 1e9 if split["h2d"] > 0 else None}
+               "host_x_read_gbs_one_step": N * M * 8 / ((split["pod_reading_host_x"] - ms) * 1e-3) / 1e9
+               if split["pod_reading_host_x"] > ms else None,
+               "same_result_as_device_x": bool(torch.equal(S_e2e, S.cpu())),
+               "copy_engine_route_outside_timed_region": copy_route}
         if not args.no_h2d_sweep:
             e2e["h2d_sweep_outside_timed_region"] = h2d_sweep(Xh, dev)
         e2e["placement"] = gpu_numa_info(local_rank)
-        del Xh, Uh, host
+        del Xh, XhT, Uh, host
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

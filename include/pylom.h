@@ -89,11 +89,15 @@ int64_t pylom_leaf_count(int64_t N, int64_t M, int64_t leaf_rows);
 /* Tree reduction of the leaf R factors (Sec. 3.1, the reduce loop of
  * Alg. 1), used by pylom_pod and pylom_tsqr.  Below 384 columns and 64
  * leaves the leaf kernels merge pairs as they finish (the second block to
- * reach a merge performs it); from 384 columns or 64 leaves on, one
- * cooperative launch after the leaves spreads every merge of a level over
- * all thread blocks, one panel of 16 columns per grid-wide step.  Both leave the same pairing, merged R
- * and node reflectors.  The environment variable PYLOM_TREE = "climb" or
- * "coop", read at each call, forces one form (testing and tuning). */
+ * reach a merge performs it); from 64 leaves at fewer than 384 columns, one
+ * cooperative launch after the leaves gives every merge one thread block
+ * that runs one 16-column block behind its two children (a pipeline over
+ * the levels); from 384 columns on, one cooperative launch spreads every
+ * merge of a level over all thread blocks, one panel of 16 columns per
+ * grid-wide step.  All three leave the same pairing, merged R and node
+ * reflectors.  The environment variable PYLOM_TREE = "climb",
+ * "pipe" or "coop", read at each call, forces one form (testing and
+ * tuning). */
 
 /* Device status recorded in a workspace by the last call that used it.
  * Synchronises `stream`, then returns the recorded pylom_status
@@ -109,7 +113,14 @@ pylom_status pylom_workspace_status(const void* ws, void* stream, int64_t* r, in
  * energy (Sec. 3.1).
  *
  *  X      in   N x M, ldx >= N, element type xtype (PYLOM_F32 or PYLOM_F64).
- *              Not modified.
+ *              Not modified.  Device memory of the current device, managed
+ *              memory, or page-locked host memory mapped into the device's
+ *              address space (cudaHostAlloc / cudaHostRegister): the leaf
+ *              kernel's prologue then reads X across the host link, so no
+ *              separate upload is needed.  Pageable host memory or another
+ *              device's memory returns PYLOM_ERR_ARG before any launch (the
+ *              same holds for w, and for the inputs of pylom_tsqr,
+ *              pylom_dmd, pylom_pod_shard_factor and pylom_spod_blocks).
  *  w      in   N cell volumes (> 0), or NULL for uniform weights.
  *  remove_mean  1: subtract the per-gridpoint temporal mean (Alg. 2).
  *  energy       keep r = min{k : sum_{i<=k} S_i^2 / sum_i S_i^2 >= energy},

@@ -296,18 +296,26 @@ def pod(X, w=None, remove_mean=True, energy=0.0, r_max=None, mode_kind=MODES_ORT
     """POD of the N x M snapshot matrix X (Alg. 2 of the paper) on the GPU.
 
     X: CUDA tensor (float32 or float64), any 2-D layout (column-major used
-    as is).  w: N cell volumes (float64) or None.  Returns U (N x r), S, VT,
-    mean.  With check=False the call stays asynchronous and U holds r_max
-    columns (r is then read later from the workspace)."""
+    as is), or a column-major page-locked host tensor (pin_memory): the leaf
+    kernel then reads it across the host link, with no separate upload.
+    w: N cell volumes (float64) or None.  Returns U (N x r), S, VT, mean.
+    With check=False the call stays asynchronous and U holds r_max columns
+    (r is then read later from the workspace)."""
     torch = _torch()
     lib = load_library()
-    X = _colmajor(X)
+    if X.device.type == "cpu":
+        if not (X.is_pinned() and X.dim() == 2 and X.stride(0) == 1 and X.stride(1) >= X.shape[0]):
+            raise ValueError("a host X must be a column-major page-locked tensor (e.g. "
+                             "torch.empty((M, N), pin_memory=True).t())")
+        dev = torch.device("cuda", torch.cuda.current_device())
+    else:
+        X = _colmajor(X)
+        dev = X.device
     N, M = X.shape
     xtype = {torch.float32: F32, torch.float64: F64}.get(X.dtype)
     if xtype is None:
         raise TypeError("X must be float32 or float64")
     r_max = M if r_max is None else int(r_max)
-    dev = X.device
     if w is not None:
         w = w.to(device=dev, dtype=torch.float64).contiguous()
     need = lib.pylom_pod_workspace_size(N, M, leaf_rows, r_max, xtype, prec)

@@ -96,6 +96,46 @@ void pylom::set_error_message(const char* fmt, ...) {
   va_end(ap);
 }
 
+bool pylom::device_readable(const void* p, const char* who, const char* what, const void** dev) {
+  cudaPointerAttributes at;
+  memset(&at, 0, sizeof(at));
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error_message("%s: %s: cudaPointerGetAttributes: %s", who, what, cudaGetErrorString(e));
+    return false;
+  }
+  int cur = 0;
+  if ((e = cudaGetDevice(&cur)) != cudaSuccess) {
+    set_error_message("%s: cudaGetDevice: %s", who, cudaGetErrorString(e));
+    return false;
+  }
+  switch (at.type) {
+    case cudaMemoryTypeDevice:
+      if (at.device != cur) {
+        set_error_message("%s: %s is memory of device %d, not of the current device %d", who, what, at.device, cur);
+        return false;
+      }
+      *dev = p;
+      return true;
+    case cudaMemoryTypeManaged:
+      *dev = p;
+      return true;
+    case cudaMemoryTypeHost:
+      if (!at.devicePointer) {
+        set_error_message("%s: %s is page-locked host memory not mapped into the device's address space", who,
+                          what);
+        return false;
+      }
+      *dev = at.devicePointer;
+      return true;
+    default:
+      set_error_message("%s: %s must be device memory or page-locked host memory (cudaHostAlloc, "
+                        "cudaHostRegister), not pageable host memory", who, what);
+      return false;
+  }
+}
+
 extern "C" const char* pylom_version(void) { return "pylom-gb300 0.1.0 (sm_103a, FP64 TSQR-SVD)"; }
 
 extern "C" const char* pylom_last_error(void) { return g_err; }
@@ -167,6 +207,12 @@ extern "C" pylom_status pylom_pod(const void* X, int64_t N, int64_t M, int64_t l
   if (!aligned256(ws) || ws_bytes < need)
     return fail(PYLOM_ERR_WORKSPACE, "pylom_pod: workspace needs %zu bytes, 256-byte aligned (got %zu)",
                 need, ws_bytes);
+  if (!device_readable(X, "pylom_pod", "X", &X)) return PYLOM_ERR_ARG;
+  if (w) {
+    const void* wd = nullptr;
+    if (!device_readable(w, "pylom_pod", "w", &wd)) return PYLOM_ERR_ARG;
+    w = (const double*)wd;
+  }
   cudaStream_t st = as_stream(stream);
   char* base = (char*)ws;
   WsHeader* hdr = (WsHeader*)base;
@@ -340,6 +386,7 @@ extern "C" pylom_status pylom_tsqr(const void* A, int64_t N, int64_t M, int64_t 
   const size_t need = tsqr_bytes(N, M, P, Q != nullptr);
   if (!aligned256(ws) || ws_bytes < need)
     return fail(PYLOM_ERR_WORKSPACE, "pylom_tsqr: workspace needs %zu bytes, 256-byte aligned", need);
+  if (!device_readable(A, "pylom_tsqr", "A", &A)) return PYLOM_ERR_ARG;
   cudaStream_t st = as_stream(stream);
   char* base = (char*)ws;
   TsqrState ts;

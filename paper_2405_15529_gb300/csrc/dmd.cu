@@ -973,6 +973,7 @@ extern "C" pylom_status pylom_dmd(const void* X, int64_t N, int64_t M, int64_t l
     set_error_message("pylom_dmd: workspace needs %zu bytes, 256-byte aligned (got %zu)", need, ws_bytes);
     return PYLOM_ERR_WORKSPACE;
   }
+  if (!device_readable(X, "pylom_dmd", "X", &X)) return PYLOM_ERR_ARG;
   const int64_t M1 = M - 1;
   cudaStream_t st = (cudaStream_t)stream;
   char* base = (char*)ws;

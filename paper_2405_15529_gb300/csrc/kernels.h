@@ -128,6 +128,14 @@ cudaError_t ensure_dyn_smem(const void* func, size_t bytes);
 // Records a message for pylom_last_error() on the calling host thread.
 void set_error_message(const char* fmt, ...);
 
+// An input the kernels read: memory of the current device, managed memory,
+// or page-locked host memory mapped into the device's address space (the
+// kernels then read it across the host link, with no separate copy).
+// *dev receives the address the kernels use.  Anything else -- pageable host
+// memory, another device's memory -- returns false with the error message
+// set, before any launch.
+bool device_readable(const void* p, const char* who, const char* what, const void** dev);
+
 // Leaf count of a problem (the rule of pylom_leaf_count; the mixed path caps
 // the automatic choice at one leaf per SM) and the shape check of the
 // tall-skinny entry points (api.cu).

@@ -134,6 +134,12 @@ extern "C" pylom_status pylom_pod_shard_factor(const void* X, int64_t N, int64_t
                       ws_bytes);
     return PYLOM_ERR_WORKSPACE;
   }
+  if (!device_readable(X, "pylom_pod_shard_factor", "X", &X)) return PYLOM_ERR_ARG;
+  if (w) {
+    const void* wd = nullptr;
+    if (!device_readable(w, "pylom_pod_shard_factor", "w", &wd)) return PYLOM_ERR_ARG;
+    w = (const double*)wd;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   ShardLayout L = shard_carve(ws, N, M, P, r_max, prec);
   cudaError_t e = cudaMemsetAsync(L.ts.hdr, 0, sizeof(WsHeader), st);

@@ -346,6 +346,7 @@ extern "C" pylom_status pylom_spod_blocks(const void* D, int64_t N, int64_t T, i
     set_error_message("pylom_spod_blocks: workspace needs %zu bytes, 256-byte aligned", need);
     return PYLOM_ERR_WORKSPACE;
   }
+  if (!device_readable(D, "pylom_spod_blocks", "D", &D)) return PYLOM_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   char* base = (char*)ws;
   double* mu = (double*)(base + sizeof(WsHeader));

@@ -2,6 +2,7 @@
 ABI) against the FP64 CPU oracle on the same seeded inputs, element by
 element, plus the full-size 4,194,304 x 256 workload against its closed-form
 construction."""
+import ctypes
 import math
 
 import numpy as np
@@ -130,6 +131,43 @@ def test_pod_graph_replay_is_repeatable(prec):
     torch.cuda.synchronize()
     assert torch.equal(first[0], U[:, :r]) and torch.equal(first[1], S) and torch.equal(first[2], VT)
     assert torch.equal(S, res.S) and torch.equal(U[:, :r], res.U)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pod_reads_page_locked_host_x(prec):
+    """X in page-locked host memory: the leaf kernel reads it across the host
+    link; the results are those of the device-resident X bit for bit."""
+    N, M = 1 << 17, 48
+    X = synth.waves(N, M, n_waves=6, noise=1e-3, seed=23)
+    dt = torch.float64 if prec == 0 else torch.float32
+    Xd = _dev(X).to(dt)
+    Xh = torch.empty((M, N), dtype=dt, pin_memory=True)
+    Xh.copy_(Xd.t())
+    Xh = Xh.t()
+    a = pg.pod(Xd, energy=0.99, prec=prec)
+    b = pg.pod(Xh, energy=0.99, prec=prec)
+    assert a.r == b.r
+    assert torch.equal(a.S, b.S) and torch.equal(a.U, b.U) and torch.equal(a.VT, b.VT)
+    assert torch.equal(a.mean, b.mean)
+
+
+def test_pod_rejects_pageable_host_x():
+    """Pageable host memory is refused on the host, before any launch."""
+    lib = pg.load_library()
+    N, M = 2048, 16
+    Xh = np.asfortranarray(np.random.default_rng(0).standard_normal((N, M)))
+    need = pg.pod_workspace_size(N, M)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    U = pg.empty_colmajor(N, M, torch.float64, "cuda")
+    S = torch.empty(M, dtype=torch.float64, device="cuda")
+    VT = pg.empty_colmajor(M, M, torch.float64, "cuda")
+    st = lib.pylom_pod(ctypes.c_void_p(Xh.ctypes.data), N, M, N, pg.F64, None, 1, 0.0, M, 0, 0, pg._dptr(U),
+                       pg._ld(U), pg._dptr(S), pg._dptr(VT), pg._ld(VT), None, None, pg.PREC_FP64, pg._dptr(ws),
+                       ws.numel(), None)
+    assert st == pg.ERR_ARG
+    assert b"pageable" in lib.pylom_last_error()
+    with pytest.raises(ValueError):
+        pg.pod(torch.from_numpy(Xh.T.copy()).t())      # a host tensor that is not page-locked
 
 
 def test_pod_zero_and_constant_rows():
