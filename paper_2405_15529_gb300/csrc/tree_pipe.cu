@@ -48,6 +48,11 @@ static __device__ bool wait_at_least(const WsHeader* h, const unsigned* flag, un
   return true;
 }
 
+// Blocks per merge: the column blocks of a merge are dealt round-robin to
+// kPipeSub thread blocks, so while one factors panel q the next applies the
+// earlier panels to block q + 1 and waits only for panel q itself.
+constexpr int kPipeSub = 2;
+
 __global__ void __launch_bounds__(kLeafThreads, 2) tree_pipe_kernel(TsqrState s) {
   extern __shared__ double smem[];
   double* sT = smem;
@@ -60,7 +65,12 @@ __global__ void __launch_bounds__(kLeafThreads, 2) tree_pipe_kernel(TsqrState s)
   const int64_t M = s.M, P = s.P, G = gridDim.x;
   const int64_t nblk = (M + kNB - 1) / kNB;
   int64_t step = 1, base = 0, m = merges_at(P, 1);
-  for (int64_t mi = blockIdx.x;; mi += G) {
+  // work unit u = merge u / kPipeSub, column blocks q = u % kPipeSub (mod
+  // kPipeSub); G is a multiple of kPipeSub, so the units of one merge run at
+  // the same time
+  for (int64_t ui = blockIdx.x;; ui += G) {
+    const int64_t mi = ui / kPipeSub;
+    const int sub = (int)(ui % kPipeSub);
     while (step < P && mi >= base + m) {
       base += m;
       step <<= 1;
@@ -80,7 +90,8 @@ __global__ void __launch_bounds__(kLeafThreads, 2) tree_pipe_kernel(TsqrState s)
     double* Rt = s.Rs + left * M * M;
     double* Rb = s.Rs + right * M * M;
     double* Tm = s.Tn + right * nblk * kSmT;
-    for (int64_t q = 0; q < nblk; ++q) {
+    const unsigned* own = s.arrive + right;   // panels of this merge factored so far
+    for (int64_t q = sub; q < nblk; q += kPipeSub) {
       const int64_t c0 = q * kNB;
       const int wc = (int)((M - c0) < kNB ? (M - c0) : kNB);
       if (tid == 0)
@@ -91,7 +102,14 @@ __global__ void __launch_bounds__(kLeafThreads, 2) tree_pipe_kernel(TsqrState s)
         return;
       }
       // left-looking update of column block q by this merge's panels 0 .. q-1
+      // (panel p factored by the unit that owns block p)
       for (int64_t p = 0; p < q; ++p) {
+        if (tid == 0) s_ok = wait_at_least(s.hdr, own, (unsigned)(p + 1));
+        __syncthreads();
+        if (!s_ok) {
+          if (tid == 0) raise_status(s.hdr, PYLOM_ERR_TIMEOUT);
+          return;
+        }
         for (int idx = tid; idx < kSmT; idx += nthr) sT[idx] = ldcg(Tm + p * kSmT + idx);
         __syncthreads();
         const int64_t k = p * kNB;
@@ -137,7 +155,8 @@ cudaError_t launch_tree_pipe(const TsqrState& s, cudaStream_t st) {
   // before the leaf kernel, which leaves them untouched when the tree runs
   // separately)
   int64_t grid = (int64_t)per * sms;
-  if (grid > s.P - 1) grid = s.P - 1;
+  if (grid > (s.P - 1) * kPipeSub) grid = (s.P - 1) * kPipeSub;
+  grid -= grid % kPipeSub;
   TsqrState a = s;
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel((const void*)tree_pipe_kernel, dim3((unsigned)grid), dim3(kLeafThreads), args,
