@@ -14,7 +14,12 @@
  * Conventions shared by every entry point
  *   - Matrices are column-major with an explicit leading dimension (ld >= rows).
  *   - Every array argument is DEVICE memory owned by the caller, unless the
- *     comment says "host".  The library never allocates: each call that needs
+ *     comment says "host".  The snapshot inputs (X of pylom_pod, pylom_tsqr,
+ *     pylom_dmd and pylom_pod_shard_factor, D of pylom_spod_blocks, and w)
+ *     may also be managed memory or page-locked host memory mapped into the
+ *     device's address space, read by the kernels across the host link;
+ *     pageable host memory or another device's memory there returns
+ *     PYLOM_ERR_ARG before any launch.  The library never allocates: each call that needs
  *     scratch takes a caller-provided device workspace whose size comes from
  *     the matching *_workspace_size query.  Workspaces must be 256-byte
  *     aligned and must not be shared by calls that may overlap on the GPU.
