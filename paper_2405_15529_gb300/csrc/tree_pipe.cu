@@ -6,22 +6,24 @@
 // level-by-level schedule of tree_coop_kernel is bound by its critical path:
 // log2(P) levels x M / kNB panel steps, each a grid barrier plus one panel
 // factorisation.  Column block q of a merged R depends only on column block
-// q of its two children, so here every merge is one thread block that walks
-// its column blocks left-looking: for block q it waits until both children
-// have published block q, applies its own panels 0 .. q-1 to the block
-// (block reflector on the FP64 tensor pipe), factors panel q and publishes
-// the block.  A parent then runs one column block behind its children, and
-// the tree costs about one merge plus one block step per level instead of
-// levels x merges' panel steps.
+// q of its two children, so here the column blocks of a merge are worked
+// left-looking by kPipeSub thread blocks in turn: for block q the owner
+// waits until both children have published block q, applies the merge's
+// panels 0 .. q-1 to it (block reflector on the FP64 tensor pipe), factors
+// panel q and publishes the block.  A parent then runs one column block
+// behind its children, and the tree costs about one merge plus one block
+// step per level instead of levels x merges' panel steps.
 //
 // Storage is that of the other two trees (left child's R on top, merged R in
 // the left slot, node reflectors in the right slot, tau by right child), so
 // the top-down pass and the adjoint read it unchanged.  The panel T factors
 // of a merge are kept in Tn (indexed by its right child) for its later
 // column blocks.  Progress: arrive[right] = column blocks of that merge that
-// are final.  Merges are numbered level by level; a block takes merges in
-// increasing number and waits only on lower-numbered ones, and the launch is
-// cooperative (all blocks resident), so the lowest unfinished merge can
+// are final.  Merges are numbered level by level, a merge's kPipeSub units
+// consecutively; a block takes units in increasing number and waits only on
+// lower-numbered merges or on a sibling unit of its own merge, which the
+// grid stride (a multiple of kPipeSub) puts in the same round; the launch is
+// cooperative (all blocks resident), so the lowest unfinished unit can
 // always proceed.  Every wait is bounded (PYLOM_ERR_TIMEOUT).
 #include "kernels.h"
 #include "reflectors.cuh"
