@@ -598,8 +598,8 @@ def c3_cpu_baseline(N, M, rmax, rows=(8192, 16384)):
 def bench_waves_1808(args, dev):
     """The 10,000,000 x 1808 float32 wake-like field (64 traveling waves,
     power-law amplitudes, noise 1e-4; 72.3 GB) through the mixed path, timed,
-    and once through the FP64 path on the same X (the comparison the mixed
-    path is judged by).  99 % energy, at most 128 modes."""
+    and once through the FP64 path on the same X (the reference its accuracy
+    and speed are stated against).  99 % energy, at most 128 modes."""
     import numpy as np
     import torch
     import paper_2405_15529_gb300 as pg
