@@ -725,7 +725,6 @@ def bench_spod(args, dev):
     [16, 128]) in one persistent launch captured in a CUDA graph."""
     import numpy as np
     import torch
-    import oracle
     import paper_2405_15529_gb300 as pg
     from paper_2405_15529_gb300 import tune
     import synth
@@ -761,12 +760,13 @@ def bench_spod(args, dev):
     # FMA lanes per SM per clock x 152 SMs x 2 flops x the maximum SM clock
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_alu = 128 * sms * 2 * 2.07e9 / 1e12
-    # oracle check on the two smallest bins (complex128 oracle on the same complex64 data)
+    # accuracy check on the two smallest bins: LAPACK's complex128 singular
+    # values of the same complex64 data (element-wise parity is the tests')
     small = np.argsort(Ns * Nbs ** 2)[:2]
     errs = []
     for f in small:
         Xf = Q[f].cpu().numpy().astype(np.complex128)
-        _, S_ref, _, _ = oracle.zsvd(Xf, k=1)
+        S_ref = np.linalg.svd(Xf, compute_uv=False)
         errs.append(float(np.max(np.abs(b.S[f].cpu().numpy() - S_ref)) / S_ref[0]))
     out = {"workload": f"spod_{args.spod_bins}bins_c64_N2^16..2^20_Nb16..128_k8", "ms_per_step": ms,
            "value": in_bytes / (ms * 1e-3) / 1e9, "unit": "GB/s of bins processed", "steps": args.spod_steps,
@@ -778,7 +778,7 @@ def bench_spod(args, dev):
                         "peak_source": "derived: 128 FP32 FMA lanes/clk/SM x %d SMs x 2 flops x 2070 MHz "
                                        "(the live FMA probe reaches %.1f TFLOP/s)" % (sms, peak_ffma),
                         "hbm_gbs_of_algorithmic_bytes": (in_bytes + out_bytes) / (ms * 1e-3) / 1e9},
-           "sigma_err_vs_oracle_smallest_bins": errs,
+           "sigma_err_vs_lapack_smallest_bins": errs,
            "leaf_rows_tuned": bool(args.tune), "tune_seconds_untimed": t_tune,
            "tuned_policy_seconds": tune_times,
            "leaf_rows_histogram": {str(h): leaf_rows.count(h) for h in sorted(set(leaf_rows))}}
