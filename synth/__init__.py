@@ -210,6 +210,13 @@ def spod_bin_sizes(n_bins: int, seed: int, n_lo: int = 1 << 16, n_hi: int = 1 <<
     return N, Nb
 
 
+def window_sizes(n_windows: int, seed: int, n_lo: int = 1 << 16, n_hi: int = 1 << 20,
+                 m_lo: int = 16, m_hi: int = 128):
+    """Sizes of a batch of real snapshot windows: N_i log-uniform in
+    [n_lo, n_hi], M_i uniform integers in [m_lo, m_hi]."""
+    return spod_bin_sizes(n_windows, seed, n_lo, n_hi, m_lo, m_hi)
+
+
 def spod_bin(N: int, Nb: int, seed: int, n_waves: int = 4, noise: float = 1e-3, dtype=np.complex64):
     """One frequency bin's matrix of block Fourier coefficients of a
     traveling-wave field (numpy, Fortran order): a traveling wave
