@@ -15,6 +15,8 @@
 // merged R in the left slot and the node reflectors in the right slot are
 // those of the last-arriver tree, so the top-down pass and the adjoint read
 // them unchanged.
+#include <atomic>
+
 #include "kernels.h"
 #include "reflectors.cuh"
 
@@ -99,12 +101,13 @@ __global__ void __launch_bounds__(kLeafThreads, 2) tree_coop_kernel(TsqrState s)
 cudaError_t launch_tree_coop(const TsqrState& s, cudaStream_t st) {
   if (s.P <= 1) return cudaSuccess;
   // co-resident grid, per device (occupancy after the shared-memory limit is raised)
-  static int grid_of[64] = {0};
+  // (atomic: calls may come from several host threads)
+  static std::atomic<int> grid_of[64];
   cudaError_t e;
   int dev = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = ensure_dyn_smem((const void*)tree_coop_kernel, kLeafSmemBytes)) != cudaSuccess) return e;
-  int grid = (dev >= 0 && dev < 64) ? grid_of[dev] : 0;
+  int grid = (dev >= 0 && dev < 64) ? grid_of[dev].load(std::memory_order_relaxed) : 0;
   if (grid == 0) {
     int sms = 0, per = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
@@ -112,7 +115,7 @@ cudaError_t launch_tree_coop(const TsqrState& s, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     if (per < 1) return cudaErrorCooperativeLaunchTooLarge;
     grid = per * sms;
-    if (dev >= 0 && dev < 64) grid_of[dev] = grid;
+    if (dev >= 0 && dev < 64) grid_of[dev].store(grid, std::memory_order_relaxed);
   }
   TsqrState a = s;
   void* args[] = {&a};

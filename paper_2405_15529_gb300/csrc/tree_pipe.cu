@@ -25,6 +25,8 @@
 // grid stride (a multiple of kPipeSub) puts in the same round; the launch is
 // cooperative (all blocks resident), so the lowest unfinished unit can
 // always proceed.  Every wait is bounded (PYLOM_ERR_TIMEOUT).
+#include <atomic>
+
 #include "kernels.h"
 #include "reflectors.cuh"
 
@@ -139,19 +141,20 @@ __global__ void __launch_bounds__(kLeafThreads, 2) tree_pipe_kernel(TsqrState s)
 
 cudaError_t launch_tree_pipe(const TsqrState& s, cudaStream_t st) {
   if (s.P <= 1) return cudaSuccess;
-  static int per_sm_of[64] = {0};
+  // (atomic: calls may come from several host threads)
+  static std::atomic<int> per_sm_of[64];
   cudaError_t e;
   int dev = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = ensure_dyn_smem((const void*)tree_pipe_kernel, kLeafSmemBytes)) != cudaSuccess) return e;
-  int per = (dev >= 0 && dev < 64) ? per_sm_of[dev] : 0;
+  int per = (dev >= 0 && dev < 64) ? per_sm_of[dev].load(std::memory_order_relaxed) : 0;
   int sms = 0;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   if (per == 0) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tree_pipe_kernel, kLeafThreads, kLeafSmemBytes);
     if (e != cudaSuccess) return e;
     if (per < 1) return cudaErrorCooperativeLaunchTooLarge;
-    if (dev >= 0 && dev < 64) per_sm_of[dev] = per;
+    if (dev >= 0 && dev < 64) per_sm_of[dev].store(per, std::memory_order_relaxed);
   }
   // the arrival counters double as progress counters (zeroed by the caller
   // before the leaf kernel, which leaves them untouched when the tree runs
